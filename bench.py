@@ -1,0 +1,381 @@
+"""Benchmark of the GB300 FIt-SNE gradient step: point-iterations/s.
+
+One "step" is one iteration of t-SNE gradient descent through the C ABI
+(bounding box, counting sort, spread, FFT convolution, Z, attraction +
+interpolation + gains/momentum update) on N points. By default the timed
+region is the whole 1000-iteration job of the N = 1,000,000, s = 2 workload
+(50-d Gaussian mixture with 100 clusters + 5% uniform background, perplexity
+30, exact k = 90 kNN affinities), starting from Y0; warm-up iterations run
+first on a scratch copy of the same job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload n1m_2d|n1m_1d|n100k_2d|n2k_2d]
+
+Under torchrun each rank runs its own independent job (its own seed): the
+method shards by job with no data-path exchange, so scaling is weak and
+value = all ranks' point-iterations / the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores instead
+(rank 0 only; a bounded number of iterations of the same job).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "point-iterations/s (FIt-SNE gradient, N=1M, 2D)"
+UNIT = "point-iterations/s"
+
+WORKLOADS = {
+    # name: (workload number, N, s, fixed intervals, schedule overrides, description)
+    "n1m_2d": (3, 1_000_000, 2, 0, dict(late_iters=250, late_alpha=4.0),
+               "N=1,000,000 50-d Gaussian mixture (100 equal clusters + 5% uniform background), "
+               "perplexity 30, exact kNN k=90, symmetrised CSR fp32 P; s=2, p=3, "
+               "N_int=max(50, ceil(width)) capped at 400; 1000-iteration schedule: "
+               "exaggeration 12 for 250, late exaggeration 4 over the final 250, lr 200"),
+    "n1m_1d": (3, 1_000_000, 1, 0, dict(late_iters=250, late_alpha=4.0),
+               "N=1,000,000 mixture as n1m_2d; s=1, p=3, N_int=max(50, ceil(width)) capped at 1000"),
+    "n100k_2d": (2, 100_000, 2, 0, {},
+                 "N=100,000 50-d Gaussian mixture, 30 clusters of Dirichlet(1) sizes, perplexity 30, "
+                 "k=90; s=2, p=3, N_int=max(50, ceil(width)); 1000 iterations"),
+    "n2k_2d": (1, 2000, 2, 50, {},
+               "N=2,000 50-d Gaussian mixture, 10 clusters, perplexity 30, k=90; s=2, p=3, "
+               "50 intervals; 1000 iterations"),
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def force_traffic(s: int, N: int):
+    """DRAM bytes per force-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "force_kernel_n1m.txt")
+    src = os.path.join(ROOT, "paper_1712_09005_gb300", "csrc", "fitsne_kernels.cu")
+    try:
+        lines = open(path).read().splitlines()
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    rec = {}
+    for ln in lines:
+        if ":" in ln and not ln.startswith("#"):
+            k, v = ln.split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("kernel_source_sha1") != sha or rec.get(f"dram_bytes_per_launch_s{s}_N{N}") is None:
+        return None
+    return float(rec[f"dram_bytes_per_launch_s{s}_N{N}"])
+
+
+def make_inputs(wl: str, job: int, device: str):
+    from paper_1712_09005_gb300 import inputs
+    num, N, s, fixed, over, desc = WORKLOADS[wl]
+    args = inputs.mixture_args(num, job=job, N=N)
+    X = inputs.mixture(**args)
+    P = inputs.affinities(X, 30.0, device=device)
+    Y0 = inputs.initial_embedding(N, s, seed=args["seed"])
+    return P, Y0
+
+
+def schedule(wl: str, n_iter: int):
+    import paper_1712_09005_gb300 as pkg
+    over = WORKLOADS[wl][4]
+    return pkg.Schedule(n_iter=n_iter, **over)
+
+
+def oracle_iterations(P, Y0, wl, sched_args, budget_s, max_iters):
+    """Times the FP64 oracle (gradient + update) from Y0 for up to budget_s."""
+    import oracle
+    num, N, s, fixed, over, desc = WORKLOADS[wl]
+    opts = oracle.InterpOptions(p=3, n_int_fixed=fixed, n_min=50,
+                                n_int_max=400 if s == 2 else 1000, use_fft=True)
+    sc = oracle.Schedule(**sched_args)
+    Y = Y0.astype(np.float64).copy()
+    uY = np.zeros_like(Y)
+    g = np.ones_like(Y)
+    Pt = P.as_tuple()
+    it = 0
+    t0 = time.perf_counter()
+    while it < max_iters:
+        out = oracle.interp_gradient(Y, Pt, alpha=oracle.alpha_at(sc, it), opts=opts)
+        oracle.step(Y, uY, g, out["dY"], sc, it)
+        it += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return it, dt, oracle.num_threads()
+
+
+def run_reference(a):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    num, N, s, fixed, over, desc = WORKLOADS[a.workload]
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    P, Y0 = make_inputs(a.workload, 0, dev)
+    sched_args = dict(n_iter=max(1000, a.steps), **over)
+    # warm-up (at most one iteration), then a bounded number of timed iterations
+    if a.warmup > 0:
+        oracle_iterations(P, Y0, a.workload, sched_args, 0.0, 1)
+    iters, dt, cores = oracle_iterations(P, Y0, a.workload, sched_args, a.ref_budget, a.steps)
+    value = N * iters / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": iters, "warmup": min(a.warmup, 1), "ms_per_step": 1e3 * dt / iters,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "N": N, "nnz": int(P.nnz), "s": s,
+                                        "iterations": [0, iters]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{iters} oracle iterations (interpolated gradient in FP64 "
+                                   f"with its radix-2 FFT, plus the update) of this job from Y0"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+    import paper_1712_09005_gb300 as pkg
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1712_09005_gb300 import build as pbuild
+    pbuild.build()
+    num, N, s, fixed, over, desc = WORKLOADS[a.workload]
+    K, W = a.steps, a.warmup
+    n_iter = max(1000, K)
+    sched = schedule(a.workload, n_iter)
+
+    P, Y0 = make_inputs(a.workload, rank, "cuda")
+    Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+    stream = torch.cuda.current_stream()
+    plan = pkg.Plan(N, s, n_intervals=fixed, stream=stream.cuda_stream)
+
+    # warm-up on a scratch copy of the job
+    Yw = torch.as_tensor(Y0.copy(), device="cuda")
+    plan.run_reset()
+    if W > 0:
+        plan.run_iters(Pd, Yw, sched, 0, W)
+    torch.cuda.synchronize()
+
+    # timed: iterations 0 .. K-1 of the job from Y0
+    Y = torch.as_tensor(Y0.copy(), device="cuda")
+    plan.run_reset()
+    plan.profile(True)
+    plan.profile_read()
+    launches0 = plan.launch_count()
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    plan.run_iters(Pd, Y, sched, 0, K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = plan.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    prof = plan.profile_read()
+    plan.profile(False)
+    info = plan.info()
+    status = plan.status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} after the timed run")
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * N * K / (ms_max / 1e3)
+
+    # roofline of the dominant kernel: attraction + interpolation + update
+    n = info["n"]
+    grid_bytes = 16 * (n ** s)
+    bytes_force = 8 * P.nnz + 4 * (N + 1) + 24 * s * N + grid_bytes
+    force_ms = prof["ms"]["force"] / max(1, prof["evals"])
+    achieved = bytes_force / (force_ms / 1e3) / 1e9
+    peak, peak_kind = peak_hbm()
+    traffic = force_traffic(s, N)
+
+    # end to end through the C ABI with host buffers (pinned): upload P and
+    # Y0, K iterations, download Y
+    e2e = None
+    if not a.no_e2e:
+        rp = torch.from_numpy(P.row_ptr).pin_memory()
+        cl = torch.from_numpy(P.col).pin_memory()
+        vl = torch.from_numpy(P.val).pin_memory()
+        Yh = torch.from_numpy(Y0.copy()).pin_memory()
+        sched_e2e = pkg.Schedule(n_iter=K, **over)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.run_host(rp.numpy(), cl.numpy(), vl.numpy(), Yh.numpy(), sched_e2e, want_kl=False)
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = 4 * (N + 1) + 8 * P.nnz + 4 * N * s
+        d2h = 4 * N * s
+        e2e = {"value": world * N * K / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+               "d2h_bytes_per_step": d2h / K,
+               "note": "one tsne_run_host call: P and Y0 uploaded once, Y downloaded once; "
+                       "bytes per step = call totals / K"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        it, dt, cores = oracle_iterations(P, Y0, a.workload, dict(n_iter=n_iter, **over),
+                                          a.cpu_seconds, 10 ** 6)
+        cpu = {"value": N * it / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{it} oracle iterations (FP64 interpolated gradient with radix-2 FFT + "
+                         f"update) of this job from Y0, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "N": N, "nnz": int(P.nnz), "s": s, "p": 3,
+                       "iterations": [0, K], "final_n_int": info["n_int"],
+                       "final_fft_len": info["fft_len"],
+                       "l2": "inputs larger than L2 (CSR of %.2f GB streamed every iteration)"
+                             % ((8 * P.nnz + 4 * (N + 1)) / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "force_kernel (attraction + interpolation + update)",
+                         "algorithmic_bytes_per_launch": bytes_force,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "phases_ms_per_iter": {k: v / max(1, prof["evals"]) for k, v in prof["ms"].items()},
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="n1m_2d")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-budget", type=float, default=120.0,
+                    help="seconds of oracle iterations the reference arm times")
+    a = ap.parse_args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,254 @@
+/*
+ * fitsne_gb300.h - C ABI of the GB300 (sm_103a) FIt-SNE gradient library.
+ *
+ * The library computes, on one GPU, the per-iteration t-SNE gradient of
+ * Linderman et al., "Efficient Algorithms for t-distributed Stochastic
+ * Neighborhood Embedding" (arXiv 1712.09005):
+ *
+ *   dC/dy_i = 4 (alpha * A_i + F_rep,i)                      (Sec. 1.1, Sec. 1.2)
+ *   A_i     = sum_j p_ij (y_i - y_j) / (1 + |y_i - y_j|^2)    (Sec. 3, sparse P)
+ *   F_rep,i = sum_{l != i} (y_l - y_i) / (1 + |y_l - y_i|^2)^2 / Z   (Eq. frep)
+ *
+ * with F_rep and Z evaluated by the interpolation / FFT scheme of Sec. 2
+ * (Algorithm 1 and its 2-D tensor version, Sec. 2.4): the points' charges are
+ * spread onto p equispaced Lagrange nodes per interval of an N_int (x N_int)
+ * box grid (Step 1), convolved with K1 = (1+r^2)^-1 and K2 = K1^2 through a
+ * zero-padded FFT of the Toeplitz matrix (Step 2), and interpolated back
+ * (Step 3); the Appendix assembles F_rep = (h_{m+1} - y(m) h_{s+2}) / Z and
+ * Z = sum_i h_1(y_i) - N (the grid cannot exclude the self term, so N is
+ * subtracted).
+ *
+ * Conventions for every entry point:
+ *   - Y, dY, uY, gains are fp32, N x s, row-major (for s = 2 the pairs
+ *     (y_i(1), y_i(2)) are adjacent). P is CSR with int32 row_ptr[N+1],
+ *     int32 col[nnz], fp32 val[nnz]; row i holds p_ij for j != i. P should be
+ *     symmetric and sum to 1 (Sec. 1.1); the library does not renormalise it.
+ *   - Unless stated otherwise, pointers are DEVICE pointers owned by the
+ *     caller; the library never frees them and never keeps them past the call.
+ *     The plan owns all scratch memory.
+ *   - Work is enqueued on the plan's stream; calls return once it is
+ *     enqueued, so results are ready after the stream is synchronised.
+ *   - Every function returns 0 (TSNE_OK) or a negative TSNE_ERR_* code; no
+ *     exception crosses the ABI. tsne_last_error_string() describes the last
+ *     failure of the calling thread. Errors detected on the device (a
+ *     non-finite coordinate) are latched in the plan and reported by
+ *     tsne_plan_status(), which synchronises the stream.
+ *   - A plan is not thread-safe; use one plan per host thread or serialise.
+ */
+#ifndef FITSNE_GB300_H
+#define FITSNE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSNE_OK 0
+#define TSNE_ERR_INVALID_ARG (-1) /* bad size, pointer, option or CSR structure */
+#define TSNE_ERR_OOM (-2)         /* device allocation failed */
+#define TSNE_ERR_NONFINITE (-3)   /* NaN or Inf met in Y (latched on the device) */
+#define TSNE_ERR_TIMEOUT (-4)     /* a bounded device wait gave up */
+#define TSNE_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define TSNE_ERR_CAPACITY (-6)    /* request exceeds what the plan was built for */
+
+typedef struct tsne_plan tsne_plan;
+
+/* Sparse affinities P (Sec. 1.1, Eq. p_ij), device CSR. */
+typedef struct {
+    const int32_t* row_ptr; /* [N+1], row_ptr[0] = 0, non-decreasing */
+    const int32_t* col;     /* [nnz], 0 <= col < N, col != row */
+    const float* val;       /* [nnz], p_ij >= 0 */
+    int64_t nnz;            /* = row_ptr[N] */
+} tsne_csr;
+
+/* Plan options; zero-initialised fields take the defaults in brackets. */
+typedef struct {
+    int32_t n_min;     /* floor of the interval rule max(n_min, ceil(width)) [50] (Sec. 2.5) */
+    int32_t n_int_max; /* cap of the rule and size of the grids [1000 if s = 1, 400 if s = 2];
+                          p * n_int_max may not exceed 3000 (s = 1) or 1200 (s = 2) */
+    void* stream;      /* cudaStream_t for all work; NULL = the legacy default stream */
+} tsne_plan_opts;
+
+/* Gradient-descent schedule (Sec. 1.2 early exaggeration, Sec. 4 late
+ * exaggeration). The momentum/gain update is not specified by the paper; the
+ * usual t-SNE rule is used:
+ *   gain <- gain + gain_inc if sign(dY) != sign(uY) else gain * gain_dec,
+ *   gain <- max(gain, min_gain); uY <- mu uY - lr gain dY; Y <- Y + uY,
+ * mu = momentum_early before mom_switch_iter, momentum_late from it on.
+ * alpha = early_alpha for iter < early_iters, late_alpha for
+ * iter >= n_iter - late_iters, 1 otherwise. */
+typedef struct {
+    int32_t n_iter;          /* total iterations of the run [1000] */
+    int32_t early_iters;     /* [250] */
+    int32_t late_iters;      /* [0] */
+    int32_t mom_switch_iter; /* [250] */
+    float early_alpha;       /* [12] */
+    float late_alpha;        /* [1] */
+    float lr;                /* [200] */
+    float momentum_early;    /* [0.5] */
+    float momentum_late;     /* [0.8] */
+    float min_gain;          /* [0.01] */
+    float gain_inc;          /* [0.2] */
+    float gain_dec;          /* [0.8] */
+} tsne_step_params;
+
+/* Box and grid of the most recent gradient evaluation (read back by
+ * tsne_plan_info, which synchronises the stream). */
+typedef struct {
+    float y_min;     /* lower corner of the box in every dimension (Sec. 2.2, 2.4) */
+    float width;     /* box side; 1 when all coordinates are equal */
+    float b;         /* interval width, width / n_int (FP32) */
+    float delta;     /* node spacing b / p (FP32) */
+    int32_t n_int;   /* intervals per dimension */
+    int32_t n;       /* nodes per dimension, p * n_int */
+    int32_t fft_len; /* padded FFT length per dimension (>= 2n) */
+    int32_t n_chunks;/* spread work items of the last iteration */
+    double Z;        /* normalisation of the last evaluation (FP64) */
+    int32_t status;  /* latched device error (TSNE_OK or TSNE_ERR_NONFINITE) */
+    int32_t pad;
+} tsne_plan_info_t;
+
+/* Library version string. */
+const char* tsne_version(void);
+
+/* Description of the last error returned on this host thread ("" if none). */
+const char* tsne_last_error_string(void);
+
+/* Fills *out with the defaults listed in tsne_step_params. */
+void tsne_step_params_default(tsne_step_params* out);
+
+/* alpha(iter) of the schedule (host helper, same rule as the device). */
+float tsne_alpha_at(const tsne_step_params* sp, int32_t iter);
+
+/*
+ * Creates a plan for N points in s dimensions (s = 1 or 2) with p nodes per
+ * interval (2 <= p <= 5; the paper recommends p = 3, Sec. 2.3).
+ * n_intervals > 0 fixes N_int per dimension (1 <= n_intervals <= n_int_max);
+ * 0 selects the automatic rule max(n_min, ceil(y_max - y_min)) each
+ * iteration (Sec. 2.5), evaluated on the device from the FP32 bounding box.
+ * Allocates all scratch for the largest grid the plan allows. N >= 2.
+ * Errors: INVALID_ARG, OOM, CUDA. On success *out owns the plan.
+ */
+int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
+                     const tsne_plan_opts* opts, tsne_plan** out);
+
+/* Frees the plan and its scratch (synchronises its stream first). NULL is a no-op. */
+int tsne_plan_destroy(tsne_plan* plan);
+
+/*
+ * Test hook: replaces the bounding box of every later evaluation by
+ * [y_min, y_min + width]^s with n_int intervals (width > 0,
+ * 1 <= n_int <= n_int_max); points outside are assigned to the nearest
+ * edge interval. width <= 0 restores the automatic box.
+ */
+int tsne_plan_set_box(tsne_plan* plan, float y_min, float width, int32_t n_int);
+
+/*
+ * The interpolated gradient (Sec. 2 + Appendix, attraction of Sec. 3):
+ * dY[i] = 4 (alpha A_i + F_rep,i) for all i, and Z (FP64) written to the
+ * DEVICE address Z_out if it is not NULL. Y: [N x s] device, read only.
+ * dY: [N x s] device, written. Y and dY must not overlap.
+ */
+int tsne_gradient(tsne_plan* plan, tsne_csr P, const float* Y, float alpha, float* dY,
+                  double* Z_out);
+
+/*
+ * One gradient-descent iteration at index iter of the schedule sp: computes
+ * the gradient with alpha(iter) and updates Y, uY and gains in place
+ * (device, [N x s] each). The new Y is produced in plan scratch and copied
+ * back, so the attraction of every point sees the old Y.
+ */
+int tsne_step(tsne_plan* plan, tsne_csr P, float* Y, float* uY, float* gains, int32_t iter,
+              const tsne_step_params* sp);
+
+/*
+ * A whole run: iterations 0 .. sp->n_iter - 1 of tsne_step starting from
+ * uY = 0 and gains = 1 (kept in plan scratch); Y (device) holds Y0 on entry
+ * and the embedding on return. If kl_out (HOST pointer) is not NULL, the KL
+ * divergence of the final embedding is computed and written (synchronises).
+ */
+int tsne_run(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
+             double* kl_out);
+
+/*
+ * The same run in pieces: tsne_run_reset sets the plan's run state to uY = 0,
+ * gains = 1; tsne_run_iters then performs iterations it_begin ..
+ * it_begin + count - 1 of the schedule sp on Y (device, in place), keeping
+ * uY and gains in the plan between calls. tsne_run equals a reset followed
+ * by tsne_run_iters(0, sp->n_iter) (and the optional KL).
+ */
+int tsne_run_reset(tsne_plan* plan);
+int tsne_run_iters(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
+                   int32_t it_begin, int32_t count);
+
+/*
+ * KL(P || Q) = sum_ij p_ij log(p_ij / q_ij) over the stored entries of P
+ * (Sec. 1.1), with Z from the interpolation scheme at Y. Per-entry logs in
+ * FP32, every sum across entries in FP64. kl_out is a HOST pointer
+ * (synchronises).
+ */
+int tsne_kl(tsne_plan* plan, tsne_csr P, const float* Y, double* kl_out);
+
+/*
+ * Same as tsne_run, but with HOST buffers: row_ptr/col/val (host, CSR as
+ * above) and Y (host, [N x s], Y0 in, embedding out) are copied to and from
+ * plan-owned device memory inside the call. The CSR is validated on the host
+ * first (INVALID_ARG on a malformed matrix). Synchronises.
+ */
+int tsne_run_host(tsne_plan* plan, const int32_t* row_ptr, const int32_t* col,
+                  const float* val, int64_t nnz, float* Y, const tsne_step_params* sp,
+                  double* kl_out);
+
+/*
+ * Checks a device CSR on the device: row_ptr[0] = 0, non-decreasing,
+ * row_ptr[N] = nnz, 0 <= col < N, col != row, finite val >= 0.
+ * Returns TSNE_OK or INVALID_ARG (synchronises).
+ */
+int tsne_validate_csr(tsne_plan* plan, tsne_csr P);
+
+/* Synchronises the plan's stream and returns the latched device status
+ * (TSNE_OK, TSNE_ERR_NONFINITE) or TSNE_ERR_CUDA; clears the latch. */
+int tsne_plan_status(tsne_plan* plan);
+
+/* Box/grid/Z of the most recent evaluation (synchronises). */
+int tsne_plan_info(tsne_plan* plan, tsne_plan_info_t* out);
+
+/*
+ * Copies an internal buffer of the most recent evaluation to HOST memory,
+ * for tests (synchronises). which:
+ *   0  spread grids w, fp32 [(s+1) x n^s], charges (1, y(1) - c, .., y(s) - c)
+ *      with c = y_min + width / 2 (the centring is exact: spreading is linear)
+ *   1  potentials at the nodes, fp32 [n^s x 4] = (h_1, h_2, h_3, h_{s+2}) with
+ *      h_3 = 0 when s = 1, the charges as in 0
+ *   2  bucket offsets, int32 [n_int^s + 1] (points per box, exclusive scan)
+ * bytes must be at least the size above; the size needed is returned in
+ * *bytes_needed (may be NULL).
+ */
+int tsne_debug_copy(tsne_plan* plan, int32_t which, void* host_dst, size_t bytes,
+                    size_t* bytes_needed);
+
+/*
+ * Phase timing (tracing). enable != 0 makes every later gradient, step or run
+ * record CUDA events on the plan's stream around its four phases:
+ *   0 bounding box, 1 counting sort + spread (Step 1),
+ *   2 FFT convolution + Z (Step 2), 3 attraction + interpolation + update
+ *   (Step 3, the force kernel).
+ * tsne_plan_profile_read synchronises, writes the summed milliseconds and
+ * the number of timed evaluations per phase to ms_out[4] / count_out[4]
+ * (HOST arrays, either may be NULL) and clears the record. enable = 0 stops
+ * recording (the record is kept until read).
+ */
+int tsne_plan_profile(tsne_plan* plan, int32_t enable);
+int tsne_plan_profile_read(tsne_plan* plan, double* ms_out, int64_t* count_out);
+
+/* Number of kernels this plan has launched since it was created (host-side
+ * count of every kernel launch the library enqueued for it). */
+int64_t tsne_plan_launch_count(const tsne_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FITSNE_GB300_H */

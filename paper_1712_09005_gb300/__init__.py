@@ -1,0 +1,284 @@
+"""GB300-native FIt-SNE gradient (arXiv 1712.09005): Python binding.
+
+The functions below carry the names of the C-ABI entry points of
+include/fitsne_gb300.h and only marshal arguments (torch tensors for device
+buffers, numpy arrays for host buffers). All arithmetic of the gradient
+(bounding box, sort, spread, FFT convolution, interpolation, attraction,
+update, Z and KL) runs in the CUDA kernels of libfitsne_gb300.so; there is
+no CPU fallback and the import fails if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, fields
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import TsneError, check
+
+__all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destroy",
+           "tsne_plan_set_box", "tsne_gradient", "tsne_step", "tsne_run", "tsne_run_reset", "tsne_run_iters", "tsne_kl",
+           "tsne_run_host", "tsne_validate_csr", "tsne_plan_status", "tsne_plan_info",
+           "tsne_debug_copy", "tsne_plan_profile", "tsne_plan_profile_read",
+           "tsne_plan_launch_count", "TsneError"]
+
+
+def lib():
+    return _abi.load()
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class DeviceCSR:
+    """P on the device: int32 row_ptr [N+1], int32 col [nnz], fp32 val [nnz]."""
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+
+    @staticmethod
+    def from_host(row_ptr, col, val, device="cuda") -> "DeviceCSR":
+        return DeviceCSR(torch.as_tensor(np.ascontiguousarray(row_ptr, np.int32), device=device),
+                         torch.as_tensor(np.ascontiguousarray(col, np.int32), device=device),
+                         torch.as_tensor(np.ascontiguousarray(val, np.float32), device=device))
+
+    @property
+    def N(self) -> int:
+        return self.row_ptr.numel() - 1
+
+    @property
+    def nnz(self) -> int:
+        return self.col.numel()
+
+    def c(self) -> _abi.tsne_csr:
+        for t, dt in ((self.row_ptr, torch.int32), (self.col, torch.int32), (self.val, torch.float32)):
+            if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+                raise TypeError("DeviceCSR tensors must be contiguous CUDA int32/int32/float32")
+        return _abi.tsne_csr(self.row_ptr.data_ptr(), self.col.data_ptr(), self.val.data_ptr(),
+                             self.nnz)
+
+
+@dataclass
+class Schedule:
+    """tsne_step_params (exaggeration schedule and optimizer constants)."""
+    n_iter: int = 1000
+    early_iters: int = 250
+    late_iters: int = 0
+    mom_switch_iter: int = 250
+    early_alpha: float = 12.0
+    late_alpha: float = 1.0
+    lr: float = 200.0
+    momentum_early: float = 0.5
+    momentum_late: float = 0.8
+    min_gain: float = 0.01
+    gain_inc: float = 0.2
+    gain_dec: float = 0.8
+
+    def c(self) -> _abi.tsne_step_params:
+        return _abi.tsne_step_params(*[getattr(self, f.name) for f in fields(self)])
+
+
+def _vec(t: torch.Tensor, N: int, s: int, name: str):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == N * s):
+        raise TypeError(f"{name} must be a contiguous CUDA float32 tensor of {N}x{s}")
+    return _ptr(t)
+
+
+# ---- functions named after the C entry points --------------------------------
+
+def tsne_plan_create(N: int, s: int, n_intervals: int = 0, p: int = 3, n_min: int = 0,
+                     n_int_max: int = 0, stream: int | None = None) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    opts = _abi.tsne_plan_opts(n_min, n_int_max, stream)
+    out = ctypes.c_void_p()
+    check(lib().tsne_plan_create(N, s, n_intervals, p, ctypes.byref(opts), ctypes.byref(out)))
+    return out
+
+
+def tsne_plan_destroy(plan) -> None:
+    check(lib().tsne_plan_destroy(plan))
+
+
+def tsne_plan_set_box(plan, y_min: float, width: float, n_int: int) -> None:
+    check(lib().tsne_plan_set_box(plan, y_min, width, n_int))
+
+
+def tsne_gradient(plan, P: DeviceCSR, Y, alpha, dY, Z=None) -> None:
+    check(lib().tsne_gradient(plan, P.c(), _ptr(Y), alpha, _ptr(dY), _ptr(Z)))
+
+
+def tsne_step(plan, P: DeviceCSR, Y, uY, gains, it: int, sched: Schedule) -> None:
+    sp = sched.c()
+    check(lib().tsne_step(plan, P.c(), _ptr(Y), _ptr(uY), _ptr(gains), it, ctypes.byref(sp)))
+
+
+def tsne_run(plan, P: DeviceCSR, Y, sched: Schedule, want_kl: bool = True):
+    sp = sched.c()
+    kl = ctypes.c_double(float("nan"))
+    check(lib().tsne_run(plan, P.c(), _ptr(Y), ctypes.byref(sp),
+                         ctypes.byref(kl) if want_kl else None))
+    return kl.value if want_kl else None
+
+
+def tsne_run_reset(plan) -> None:
+    check(lib().tsne_run_reset(plan))
+
+
+def tsne_run_iters(plan, P: DeviceCSR, Y, sched: Schedule, it_begin: int, count: int) -> None:
+    sp = sched.c()
+    check(lib().tsne_run_iters(plan, P.c(), _ptr(Y), ctypes.byref(sp), it_begin, count))
+
+
+def tsne_kl(plan, P: DeviceCSR, Y) -> float:
+    kl = ctypes.c_double()
+    check(lib().tsne_kl(plan, P.c(), _ptr(Y), ctypes.byref(kl)))
+    return kl.value
+
+
+def tsne_run_host(plan, row_ptr: np.ndarray, col: np.ndarray, val: np.ndarray, Y: np.ndarray,
+                  sched: Schedule, want_kl: bool = True):
+    """Y (host float32, N x s) is overwritten with the embedding."""
+    for a, dt in ((row_ptr, np.int32), (col, np.int32), (val, np.float32), (Y, np.float32)):
+        if a.dtype != dt or not a.flags.c_contiguous:
+            raise TypeError("host arrays must be contiguous int32/int32/float32/float32")
+    sp = sched.c()
+    kl = ctypes.c_double(float("nan"))
+    P_ = ctypes.c_void_p
+    check(lib().tsne_run_host(plan, P_(row_ptr.ctypes.data), P_(col.ctypes.data),
+                              P_(val.ctypes.data), len(col), P_(Y.ctypes.data), ctypes.byref(sp),
+                              ctypes.byref(kl) if want_kl else None))
+    return kl.value if want_kl else None
+
+
+def tsne_validate_csr(plan, P: DeviceCSR) -> None:
+    check(lib().tsne_validate_csr(plan, P.c()))
+
+
+def tsne_plan_status(plan) -> int:
+    return int(lib().tsne_plan_status(plan))
+
+
+def tsne_plan_info(plan) -> dict:
+    info = _abi.tsne_plan_info_t()
+    check(lib().tsne_plan_info(plan, ctypes.byref(info)))
+    return {f[0]: getattr(info, f[0]) for f in info._fields_ if f[0] != "pad"}
+
+
+def tsne_debug_copy(plan, which: int, s: int) -> np.ndarray:
+    need = ctypes.c_size_t()
+    check(lib().tsne_debug_copy(plan, which, None, 0, ctypes.byref(need)))
+    if which == 2:
+        out = np.empty(need.value // 4, dtype=np.int32)
+    elif which == 1:
+        out = np.empty((need.value // 16, 4), dtype=np.float32)
+    else:
+        out = np.empty(need.value // 4, dtype=np.float32)
+    check(lib().tsne_debug_copy(plan, which, ctypes.c_void_p(out.ctypes.data), out.nbytes, None))
+    return out
+
+
+PHASES = ("box", "sort_spread", "fft_conv", "force")
+
+
+def tsne_plan_profile(plan, enable: bool) -> None:
+    check(lib().tsne_plan_profile(plan, 1 if enable else 0))
+
+
+def tsne_plan_profile_read(plan) -> dict:
+    ms = (ctypes.c_double * 4)()
+    cnt = (ctypes.c_int64 * 4)()
+    check(lib().tsne_plan_profile_read(plan, ms, cnt))
+    return {"ms": dict(zip(PHASES, list(ms))), "evals": int(cnt[0])}
+
+
+def tsne_plan_launch_count(plan) -> int:
+    return int(lib().tsne_plan_launch_count(plan))
+
+
+# ---- convenience object -------------------------------------------------------
+
+class Plan:
+    """Owns a tsne_plan; methods forward to the functions above."""
+
+    def __init__(self, N: int, s: int, n_intervals: int = 0, p: int = 3, n_min: int = 0,
+                 n_int_max: int = 0, stream: int | None = None):
+        self.N, self.s = N, s
+        self.handle = tsne_plan_create(N, s, n_intervals, p, n_min, n_int_max, stream)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            tsne_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_box(self, y_min: float, width: float, n_int: int):
+        tsne_plan_set_box(self.handle, y_min, width, n_int)
+
+    def gradient(self, P: DeviceCSR, Y: torch.Tensor, alpha: float = 1.0, dY=None, Z=None):
+        _vec(Y, self.N, self.s, "Y")
+        if dY is None:
+            dY = torch.empty_like(Y)
+        if Z is None:
+            Z = torch.empty(1, dtype=torch.float64, device=Y.device)
+        tsne_gradient(self.handle, P, Y, alpha, dY, Z)
+        return dY, Z
+
+    def step(self, P: DeviceCSR, Y, uY, gains, it: int, sched: Schedule):
+        for t, nm in ((Y, "Y"), (uY, "uY"), (gains, "gains")):
+            _vec(t, self.N, self.s, nm)
+        tsne_step(self.handle, P, Y, uY, gains, it, sched)
+
+    def run(self, P: DeviceCSR, Y: torch.Tensor, sched: Schedule, want_kl: bool = True):
+        _vec(Y, self.N, self.s, "Y")
+        return tsne_run(self.handle, P, Y, sched, want_kl)
+
+    def run_reset(self):
+        tsne_run_reset(self.handle)
+
+    def run_iters(self, P: DeviceCSR, Y: torch.Tensor, sched: Schedule, it_begin: int, count: int):
+        _vec(Y, self.N, self.s, "Y")
+        tsne_run_iters(self.handle, P, Y, sched, it_begin, count)
+
+    def kl(self, P: DeviceCSR, Y: torch.Tensor) -> float:
+        _vec(Y, self.N, self.s, "Y")
+        return tsne_kl(self.handle, P, Y)
+
+    def run_host(self, row_ptr, col, val, Y: np.ndarray, sched: Schedule, want_kl: bool = True):
+        return tsne_run_host(self.handle, row_ptr, col, val, Y, sched, want_kl)
+
+    def validate(self, P: DeviceCSR):
+        tsne_validate_csr(self.handle, P)
+
+    def status(self) -> int:
+        return tsne_plan_status(self.handle)
+
+    def info(self) -> dict:
+        return tsne_plan_info(self.handle)
+
+    def debug(self, which: int) -> np.ndarray:
+        return tsne_debug_copy(self.handle, which, self.s)
+
+    def profile(self, enable: bool = True):
+        tsne_plan_profile(self.handle, enable)
+
+    def profile_read(self) -> dict:
+        return tsne_plan_profile_read(self.handle)
+
+    def launch_count(self) -> int:
+        return tsne_plan_launch_count(self.handle)

@@ -1,0 +1,589 @@
+// C ABI of the GB300 FIt-SNE library (declared in include/fitsne_gb300.h):
+// plan construction (scratch sized for the largest grid the plan allows,
+// the FFT length table and its twiddles), argument validation, and the
+// per-iteration launch sequence
+//   box -> count/scan/scatter/spread -> rows/cols/rows FFT (+ Z) -> forces.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <vector>
+
+#include "fitsne_internal.cuh"
+
+using fitsne::FftEntry;
+using fitsne::Params;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(TSNE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+    } while (0)
+
+bool smooth5(int L) {
+    int x = L;
+    for (int f : {2, 3, 5})
+        while (x % f == 0) x /= f;
+    return x == 1;
+}
+
+// Even 5-smooth lengths from 4 to the first one >= l_need, with radix plans.
+std::vector<FftEntry> fft_table(int l_need, int* tw_total) {
+    std::vector<FftEntry> t;
+    int off = 0;
+    for (int L = 4;; L += 2) {
+        if (!smooth5(L)) continue;
+        FftEntry e{};
+        e.L = L;
+        e.tw_off = off;
+        int x = L, k = 0;
+        while (x % 4 == 0) { e.radix[k++] = 4; x /= 4; }
+        while (x % 2 == 0) { e.radix[k++] = 2; x /= 2; }
+        while (x % 3 == 0) { e.radix[k++] = 3; x /= 3; }
+        while (x % 5 == 0) { e.radix[k++] = 5; x /= 5; }
+        e.nst = k;
+        t.push_back(e);
+        off += L;
+        if (L >= l_need) break;
+    }
+    *tw_total = off;
+    return t;
+}
+
+template <typename T>
+int dalloc(T** p, size_t count, const char* what) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? TSNE_ERR_OOM : TSNE_ERR_CUDA,
+                    "cudaMalloc of %s (%zu bytes): %s", what, count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    return TSNE_OK;
+}
+
+// Phase event record of the tracing hooks: five events per timed evaluation
+// (start, after box, after sort+spread, after FFT, after forces).
+struct Prof {
+    std::vector<cudaEvent_t> free_ev;
+    std::vector<std::array<cudaEvent_t, 5>> recs;
+};
+
+Prof* prof_of(tsne_plan* pl) {
+    if (!pl->prof) pl->prof = new Prof();
+    return static_cast<Prof*>(pl->prof);
+}
+
+cudaEvent_t take_event(Prof* pr) {
+    cudaEvent_t e = nullptr;
+    if (!pr->free_ev.empty()) {
+        e = pr->free_ev.back();
+        pr->free_ev.pop_back();
+    } else {
+        cudaEventCreate(&e);
+    }
+    return e;
+}
+
+void prof_begin(tsne_plan* pl) {
+    if (!pl->profiling) return;
+    Prof* pr = prof_of(pl);
+    std::array<cudaEvent_t, 5> a;
+    for (auto& e : a) e = take_event(pr);
+    pr->recs.push_back(a);
+    cudaEventRecord(a[0], pl->stream);
+}
+
+void prof_mark(tsne_plan* pl, int k) {
+    if (!pl->profiling || !pl->prof) return;
+    Prof* pr = static_cast<Prof*>(pl->prof);
+    if (!pr->recs.empty()) cudaEventRecord(pr->recs.back()[k], pl->stream);
+}
+
+void free_prof(tsne_plan* pl) {
+    if (!pl->prof) return;
+    Prof* pr = static_cast<Prof*>(pl->prof);
+    for (auto& a : pr->recs)
+        for (auto e : a) cudaEventDestroy(e);
+    for (auto e : pr->free_ev) cudaEventDestroy(e);
+    delete pr;
+    pl->prof = nullptr;
+}
+
+void free_plan(tsne_plan* pl) {
+    free_prof(pl);
+    void* ptrs[] = {pl->params,    pl->box_partial, pl->tickets,     pl->counts,     pl->box_start,
+                    pl->cursor,    pl->chunk_start, pl->chunk_box,   pl->block_pts,  pl->block_chunks,
+                    pl->sorted_y,  pl->w,           pl->spec,        pl->hgrid,      pl->z_partial,
+                    pl->kl_partial, pl->kl_out_dev, pl->valid_flag,  pl->y_next,     pl->uY_run,
+                    pl->gains_run, pl->fft_table,   pl->twiddles,    pl->h_row_ptr,  pl->h_col,
+                    pl->h_val,     pl->h_Y};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete pl;
+}
+
+int check_plan(const tsne_plan* pl) {
+    if (!pl) return fail(TSNE_ERR_INVALID_ARG, "plan is NULL");
+    return TSNE_OK;
+}
+
+int check_csr(const tsne_plan* pl, const tsne_csr& P) {
+    if (!P.row_ptr || (P.nnz > 0 && (!P.col || !P.val)))
+        return fail(TSNE_ERR_INVALID_ARG, "CSR pointer is NULL");
+    if (P.nnz < 0 || P.nnz > INT32_MAX)
+        return fail(TSNE_ERR_INVALID_ARG, "nnz %lld out of range [0, 2^31)", (long long)P.nnz);
+    (void)pl;
+    return TSNE_OK;
+}
+
+int check_vec(const tsne_plan* pl, const void* p, const char* name) {
+    if (!p) return fail(TSNE_ERR_INVALID_ARG, "%s is NULL", name);
+    if ((reinterpret_cast<uintptr_t>(p) & (pl->s == 2 ? 7 : 3)) != 0)
+        return fail(TSNE_ERR_INVALID_ARG, "%s is not %d-byte aligned", name, pl->s == 2 ? 8 : 4);
+    return TSNE_OK;
+}
+
+float alpha_at(const tsne_step_params* sp, int it) {
+    if (it < sp->early_iters) return sp->early_alpha;
+    if (sp->late_iters > 0 && it >= sp->n_iter - sp->late_iters) return sp->late_alpha;
+    return 1.0f;
+}
+
+// The repulsive half of an iteration: box, sort, spread, convolution, Z.
+// With timed set and tracing on, phase events 0..3 are recorded around it;
+// the caller records event 4 after the force kernel.
+int enqueue_field(tsne_plan* pl, const float* Y, double* Z_out, bool timed) {
+    if (timed) prof_begin(pl);
+    CU(fitsne::launch_box(pl, Y), "box kernel launch");
+    if (timed) prof_mark(pl, 1);
+    CU(fitsne::launch_sort_and_spread(pl, Y), "sort/spread launch");
+    if (timed) prof_mark(pl, 2);
+    CU(fitsne::launch_convolution(pl, Z_out), "FFT launch");
+    if (timed) prof_mark(pl, 3);
+    return TSNE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tsne_version(void) { return "fitsne-gb300 0.1 (sm_103a)"; }
+
+const char* tsne_last_error_string(void) { return g_err; }
+
+void tsne_step_params_default(tsne_step_params* out) {
+    if (!out) return;
+    out->n_iter = 1000;
+    out->early_iters = 250;
+    out->late_iters = 0;
+    out->mom_switch_iter = 250;
+    out->early_alpha = 12.0f;
+    out->late_alpha = 1.0f;
+    out->lr = 200.0f;
+    out->momentum_early = 0.5f;
+    out->momentum_late = 0.8f;
+    out->min_gain = 0.01f;
+    out->gain_inc = 0.2f;
+    out->gain_dec = 0.8f;
+}
+
+float tsne_alpha_at(const tsne_step_params* sp, int32_t iter) { return sp ? alpha_at(sp, iter) : 1.0f; }
+
+int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
+                     const tsne_plan_opts* opts, tsne_plan** out) {
+    g_err[0] = 0;
+    if (!out) return fail(TSNE_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (s != 1 && s != 2) return fail(TSNE_ERR_INVALID_ARG, "s must be 1 or 2 (got %d)", s);
+    if (p < 2 || p > 5) return fail(TSNE_ERR_INVALID_ARG, "p must be in [2, 5] (got %d)", p);
+    if (N < 2 || N > INT32_MAX / 2) return fail(TSNE_ERR_INVALID_ARG, "N must be in [2, 2^30) (got %lld)", (long long)N);
+    tsne_plan_opts o{};
+    if (opts) o = *opts;
+    int n_min = o.n_min > 0 ? o.n_min : 50;
+    int n_int_max = o.n_int_max > 0 ? o.n_int_max : (s == 2 ? 400 : 1000);
+    // grid limits: 2-D column FFTs keep ten length-L columns in shared memory
+    const int n_cap = (s == 2) ? 1200 : 3000;
+    if ((int64_t)p * n_int_max > n_cap)
+        return fail(TSNE_ERR_INVALID_ARG, "p * n_int_max = %d exceeds %d nodes per dimension",
+                    p * n_int_max, n_cap);
+    if (n_intervals < 0 || n_intervals > n_int_max)
+        return fail(TSNE_ERR_INVALID_ARG, "n_intervals %d outside [0, %d]", n_intervals, n_int_max);
+    if (n_min > n_int_max) n_min = n_int_max;
+
+    tsne_plan* pl = new tsne_plan();
+    memset(pl, 0, sizeof(*pl));
+    pl->N = N;
+    pl->s = s;
+    pl->p = p;
+    pl->n_int_fixed = n_intervals;
+    pl->n_min = n_min;
+    pl->n_int_max = n_int_max;
+    pl->stream = (cudaStream_t)o.stream;
+    pl->n_max = p * n_int_max;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) { free_plan(pl); return cuda_fail(ce, "device query"); }
+
+    int tw_total = 0;
+    std::vector<FftEntry> tab = fft_table(2 * pl->n_max, &tw_total);
+    pl->n_fft = (int)tab.size();
+    pl->L_max = tab.back().L;
+    std::vector<float2> tw(tw_total);
+    for (const FftEntry& e : tab)
+        for (int j = 0; j < e.L; ++j) {
+            const double a = -2.0 * M_PI * (double)j / (double)e.L;
+            tw[e.tw_off + j] = make_float2((float)cos(a), (float)sin(a));
+        }
+
+    pl->n_boxes_max = (s == 2) ? (int64_t)n_int_max * n_int_max : n_int_max;
+    pl->scan_blocks = (int)((pl->n_boxes_max + fitsne::kScanBlock - 1) / fitsne::kScanBlock);
+    pl->chunk_cap = N / fitsne::kChunk + std::min<int64_t>(N, pl->n_boxes_max) + 1;
+    const int64_t G = (s == 2) ? (int64_t)pl->n_max * pl->n_max : pl->n_max;
+    const int kl_blocks = 4 * pl->sm_count;
+
+    int rc = TSNE_OK;
+#define ALLOC(ptr, count) \
+    if (rc == TSNE_OK) rc = dalloc(&pl->ptr, (size_t)(count), #ptr)
+    ALLOC(params, 1);
+    ALLOC(box_partial, 2 * fitsne::kBoxBlocks);
+    ALLOC(tickets, 4);
+    ALLOC(counts, pl->n_boxes_max);
+    ALLOC(box_start, pl->n_boxes_max + 1);
+    ALLOC(cursor, pl->n_boxes_max);
+    ALLOC(chunk_start, pl->n_boxes_max + 1);
+    ALLOC(chunk_box, pl->chunk_cap);
+    ALLOC(block_pts, pl->scan_blocks);
+    ALLOC(block_chunks, pl->scan_blocks);
+    ALLOC(sorted_y, N * s);
+    ALLOC(w, (s + 1) * G);
+    if (s == 2) ALLOC(spec, 3 * (int64_t)pl->n_max * pl->L_max);
+    ALLOC(hgrid, G);
+    ALLOC(z_partial, pl->n_max);
+    ALLOC(kl_partial, 2 * kl_blocks);
+    ALLOC(kl_out_dev, 1);
+    ALLOC(valid_flag, 1);
+    ALLOC(y_next, N * s);
+    ALLOC(uY_run, N * s);
+    ALLOC(gains_run, N * s);
+    ALLOC(fft_table, tab.size());
+    ALLOC(twiddles, tw_total);
+#undef ALLOC
+    if (rc != TSNE_OK) { free_plan(pl); return rc; }
+    cudaStream_t st = pl->stream;
+    ce = cudaMemsetAsync(pl->params, 0, sizeof(Params), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(pl->tickets, 0, 4 * sizeof(unsigned), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(pl->counts, 0, pl->n_boxes_max * sizeof(int32_t), st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(pl->fft_table, tab.data(), tab.size() * sizeof(FftEntry),
+                             cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(pl->twiddles, tw.data(), tw.size() * sizeof(float2),
+                             cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = fitsne::fft_configure(pl);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) { free_plan(pl); return cuda_fail(ce, "plan initialisation"); }
+    *out = pl;
+    return TSNE_OK;
+}
+
+int tsne_plan_destroy(tsne_plan* plan) {
+    if (!plan) return TSNE_OK;
+    cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+    return TSNE_OK;
+}
+
+int tsne_plan_set_box(tsne_plan* plan, float y_min, float width, int32_t n_int) {
+    if (int rc = check_plan(plan)) return rc;
+    if (!(width > 0.0f)) {
+        plan->force_box = 0;
+        return TSNE_OK;
+    }
+    if (!isfinite(y_min) || !isfinite(width) || n_int < 1 || n_int > plan->n_int_max)
+        return fail(TSNE_ERR_INVALID_ARG, "invalid box (y_min %g, width %g, n_int %d)", y_min,
+                    width, n_int);
+    plan->force_box = 1;
+    plan->force_y_min = y_min;
+    plan->force_width = width;
+    plan->force_n_int = n_int;
+    return TSNE_OK;
+}
+
+int tsne_gradient(tsne_plan* plan, tsne_csr P, const float* Y, float alpha, float* dY,
+                  double* Z_out) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_csr(plan, P)) return rc;
+    if (int rc = check_vec(plan, Y, "Y")) return rc;
+    if (int rc = check_vec(plan, dY, "dY")) return rc;
+    if (Y == dY) return fail(TSNE_ERR_INVALID_ARG, "Y and dY must not alias");
+    if (int rc = enqueue_field(plan, Y, Z_out, true)) return rc;
+    CU(fitsne::launch_gradient(plan, P, Y, alpha, dY), "force kernel launch");
+    prof_mark(plan, 4);
+    return TSNE_OK;
+}
+
+static int step_into(tsne_plan* plan, const tsne_csr& P, const float* Y, float* Y_new,
+                     float* uY, float* gains, int32_t iter, const tsne_step_params* sp) {
+    if (int rc = enqueue_field(plan, Y, nullptr, true)) return rc;
+    const float mom = iter < sp->mom_switch_iter ? sp->momentum_early : sp->momentum_late;
+    CU(fitsne::launch_step(plan, P, Y, Y_new, uY, gains, alpha_at(sp, iter), mom, sp->lr,
+                           sp->min_gain, sp->gain_inc, sp->gain_dec),
+       "step kernel launch");
+    prof_mark(plan, 4);
+    return TSNE_OK;
+}
+
+int tsne_step(tsne_plan* plan, tsne_csr P, float* Y, float* uY, float* gains, int32_t iter,
+              const tsne_step_params* sp) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_csr(plan, P)) return rc;
+    if (int rc = check_vec(plan, Y, "Y")) return rc;
+    if (int rc = check_vec(plan, uY, "uY")) return rc;
+    if (int rc = check_vec(plan, gains, "gains")) return rc;
+    if (!sp) return fail(TSNE_ERR_INVALID_ARG, "step params are NULL");
+    if (int rc = step_into(plan, P, Y, plan->y_next, uY, gains, iter, sp)) return rc;
+    CU(cudaMemcpyAsync(Y, plan->y_next, sizeof(float) * plan->N * plan->s,
+                       cudaMemcpyDeviceToDevice, plan->stream),
+       "copy of the new Y");
+    return TSNE_OK;
+}
+
+static int reset_run_state(tsne_plan* plan) {
+    const int64_t M = plan->N * plan->s;
+    CU(cudaMemsetAsync(plan->uY_run, 0, sizeof(float) * M, plan->stream), "uY reset");
+    CU(fitsne::launch_fill(plan, plan->gains_run, 1.0f, M), "gains reset");
+    return TSNE_OK;
+}
+
+// Iterations it0 .. it0+count-1, ping-ponging Y with plan scratch; the
+// result ends in Y.
+static int run_iters(tsne_plan* plan, const tsne_csr& P, float* Y, const tsne_step_params* sp,
+                     int it0, int count) {
+    float* cur = Y;
+    float* nxt = plan->y_next;
+    for (int it = it0; it < it0 + count; ++it) {
+        if (int rc = step_into(plan, P, cur, nxt, plan->uY_run, plan->gains_run, it, sp)) return rc;
+        std::swap(cur, nxt);
+    }
+    if (cur != Y)
+        CU(cudaMemcpyAsync(Y, cur, sizeof(float) * plan->N * plan->s, cudaMemcpyDeviceToDevice,
+                           plan->stream),
+           "copy of the final Y");
+    return TSNE_OK;
+}
+
+static int run_device(tsne_plan* plan, const tsne_csr& P, float* Y, const tsne_step_params* sp,
+                      double* kl_out) {
+    if (int rc = reset_run_state(plan)) return rc;
+    if (int rc = run_iters(plan, P, Y, sp, 0, sp->n_iter)) return rc;
+    if (kl_out) return tsne_kl(plan, P, Y, kl_out);
+    return TSNE_OK;
+}
+
+int tsne_run_reset(tsne_plan* plan) {
+    if (int rc = check_plan(plan)) return rc;
+    return reset_run_state(plan);
+}
+
+int tsne_run_iters(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
+                   int32_t it_begin, int32_t count) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_csr(plan, P)) return rc;
+    if (int rc = check_vec(plan, Y, "Y")) return rc;
+    if (!sp || it_begin < 0 || count < 0) return fail(TSNE_ERR_INVALID_ARG, "invalid iteration range");
+    return run_iters(plan, P, Y, sp, it_begin, count);
+}
+
+int tsne_run(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp, double* kl_out) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_csr(plan, P)) return rc;
+    if (int rc = check_vec(plan, Y, "Y")) return rc;
+    if (!sp || sp->n_iter < 0) return fail(TSNE_ERR_INVALID_ARG, "invalid step params");
+    return run_device(plan, P, Y, sp, kl_out);
+}
+
+int tsne_kl(tsne_plan* plan, tsne_csr P, const float* Y, double* kl_out) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_csr(plan, P)) return rc;
+    if (int rc = check_vec(plan, Y, "Y")) return rc;
+    if (!kl_out) return fail(TSNE_ERR_INVALID_ARG, "kl_out is NULL");
+    if (int rc = enqueue_field(plan, Y, nullptr, false)) return rc;
+    CU(fitsne::launch_kl(plan, P, Y), "KL kernel launch");
+    CU(cudaMemcpyAsync(kl_out, plan->kl_out_dev, sizeof(double), cudaMemcpyDeviceToHost,
+                       plan->stream),
+       "KL read-back");
+    CU(cudaStreamSynchronize(plan->stream), "KL synchronise");
+    return TSNE_OK;
+}
+
+int tsne_validate_csr(tsne_plan* plan, tsne_csr P) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_csr(plan, P)) return rc;
+    CU(cudaMemsetAsync(plan->valid_flag, 0, sizeof(int32_t), plan->stream), "flag reset");
+    CU(fitsne::launch_validate(plan, P), "validate launch");
+    int32_t flag = 0;
+    CU(cudaMemcpyAsync(&flag, plan->valid_flag, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       plan->stream),
+       "flag read-back");
+    CU(cudaStreamSynchronize(plan->stream), "validate synchronise");
+    if (flag) return fail(TSNE_ERR_INVALID_ARG, "malformed CSR (row_ptr, col or val out of range)");
+    return TSNE_OK;
+}
+
+int tsne_run_host(tsne_plan* plan, const int32_t* row_ptr, const int32_t* col, const float* val,
+                  int64_t nnz, float* Y, const tsne_step_params* sp, double* kl_out) {
+    if (int rc = check_plan(plan)) return rc;
+    if (!row_ptr || !Y || (nnz > 0 && (!col || !val)) || !sp)
+        return fail(TSNE_ERR_INVALID_ARG, "NULL host pointer");
+    if (nnz < 0 || nnz > INT32_MAX) return fail(TSNE_ERR_INVALID_ARG, "nnz out of range");
+    const int64_t N = plan->N;
+    if (row_ptr[0] != 0 || row_ptr[N] != nnz)
+        return fail(TSNE_ERR_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[N] = nnz");
+    if (nnz > plan->host_nnz_cap) {
+        if (plan->h_col) cudaFree(plan->h_col);
+        if (plan->h_val) cudaFree(plan->h_val);
+        plan->h_col = nullptr;
+        plan->h_val = nullptr;
+        plan->host_nnz_cap = 0;
+        if (int rc = dalloc(&plan->h_col, nnz, "host-path col")) return rc;
+        if (int rc = dalloc(&plan->h_val, nnz, "host-path val")) return rc;
+        plan->host_nnz_cap = nnz;
+    }
+    if (!plan->h_row_ptr)
+        if (int rc = dalloc(&plan->h_row_ptr, N + 1, "host-path row_ptr")) return rc;
+    if (!plan->h_Y)
+        if (int rc = dalloc(&plan->h_Y, N * plan->s, "host-path Y")) return rc;
+    cudaStream_t st = plan->stream;
+    CU(cudaMemcpyAsync(plan->h_row_ptr, row_ptr, sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice, st), "row_ptr upload");
+    if (nnz > 0) {
+        CU(cudaMemcpyAsync(plan->h_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st), "col upload");
+        CU(cudaMemcpyAsync(plan->h_val, val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st), "val upload");
+    }
+    CU(cudaMemcpyAsync(plan->h_Y, Y, sizeof(float) * N * plan->s, cudaMemcpyHostToDevice, st), "Y upload");
+    tsne_csr P{plan->h_row_ptr, plan->h_col, plan->h_val, nnz};
+    if (int rc = tsne_validate_csr(plan, P)) return rc;
+    if (int rc = run_device(plan, P, plan->h_Y, sp, kl_out)) return rc;
+    CU(cudaMemcpyAsync(Y, plan->h_Y, sizeof(float) * N * plan->s, cudaMemcpyDeviceToHost, st), "Y download");
+    CU(cudaStreamSynchronize(st), "run synchronise");
+    return TSNE_OK;
+}
+
+int tsne_plan_status(tsne_plan* plan) {
+    if (int rc = check_plan(plan)) return rc;
+    int32_t err = 0;
+    CU(cudaMemcpyAsync(&err, &plan->params->error, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       plan->stream),
+       "status read-back");
+    CU(cudaStreamSynchronize(plan->stream), "status synchronise");
+    if (err) {
+        CU(cudaMemsetAsync(&plan->params->error, 0, sizeof(int32_t), plan->stream), "status clear");
+        CU(cudaStreamSynchronize(plan->stream), "status synchronise");
+        return fail(err, "non-finite coordinate in Y");
+    }
+    return TSNE_OK;
+}
+
+int tsne_plan_info(tsne_plan* plan, tsne_plan_info_t* out) {
+    if (int rc = check_plan(plan)) return rc;
+    if (!out) return fail(TSNE_ERR_INVALID_ARG, "out is NULL");
+    Params P;
+    CU(cudaMemcpyAsync(&P, plan->params, sizeof(Params), cudaMemcpyDeviceToHost, plan->stream),
+       "params read-back");
+    CU(cudaStreamSynchronize(plan->stream), "info synchronise");
+    out->y_min = P.y_min;
+    out->width = P.width;
+    out->b = P.b;
+    out->delta = P.delta;
+    out->n_int = P.n_int;
+    out->n = P.n;
+    out->fft_len = P.L;
+    out->n_chunks = P.n_chunks;
+    out->Z = P.Z;
+    out->status = P.error;
+    out->pad = 0;
+    return TSNE_OK;
+}
+
+int tsne_debug_copy(tsne_plan* plan, int32_t which, void* host_dst, size_t bytes,
+                    size_t* bytes_needed) {
+    if (int rc = check_plan(plan)) return rc;
+    Params P;
+    CU(cudaMemcpyAsync(&P, plan->params, sizeof(Params), cudaMemcpyDeviceToHost, plan->stream),
+       "params read-back");
+    CU(cudaStreamSynchronize(plan->stream), "debug synchronise");
+    const int64_t G = (plan->s == 2) ? (int64_t)P.n * P.n : P.n;
+    const void* src = nullptr;
+    size_t need = 0;
+    switch (which) {
+        case 0: src = plan->w; need = sizeof(float) * (plan->s + 1) * G; break;
+        case 1: src = plan->hgrid; need = sizeof(float4) * G; break;
+        case 2: src = plan->box_start; need = sizeof(int32_t) * (P.n_boxes + 1); break;
+        default: return fail(TSNE_ERR_INVALID_ARG, "unknown buffer %d", which);
+    }
+    if (bytes_needed) *bytes_needed = need;
+    if (!host_dst) return TSNE_OK;
+    if (bytes < need) return fail(TSNE_ERR_INVALID_ARG, "buffer too small (%zu < %zu)", bytes, need);
+    CU(cudaMemcpyAsync(host_dst, src, need, cudaMemcpyDeviceToHost, plan->stream), "debug copy");
+    CU(cudaStreamSynchronize(plan->stream), "debug synchronise");
+    return TSNE_OK;
+}
+
+int tsne_plan_profile(tsne_plan* plan, int32_t enable) {
+    if (int rc = check_plan(plan)) return rc;
+    plan->profiling = enable != 0;
+    return TSNE_OK;
+}
+
+int tsne_plan_profile_read(tsne_plan* plan, double* ms_out, int64_t* count_out) {
+    if (int rc = check_plan(plan)) return rc;
+    double ms[4] = {0, 0, 0, 0};
+    int64_t cnt = 0;
+    CU(cudaStreamSynchronize(plan->stream), "profile synchronise");
+    if (plan->prof) {
+        Prof* pr = static_cast<Prof*>(plan->prof);
+        for (auto& a : pr->recs) {
+            for (int k = 0; k < 4; ++k) {
+                float t = 0.0f;
+                CU(cudaEventElapsedTime(&t, a[k], a[k + 1]), "event elapsed time");
+                ms[k] += t;
+            }
+            ++cnt;
+            for (auto e : a) pr->free_ev.push_back(e);
+        }
+        pr->recs.clear();
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (ms_out) ms_out[k] = ms[k];
+        if (count_out) count_out[k] = cnt;
+    }
+    return TSNE_OK;
+}
+
+int64_t tsne_plan_launch_count(const tsne_plan* plan) { return plan ? plan->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,468 @@
+// Step 2 of the interpolation scheme: the Toeplitz (2-D: block-Toeplitz)
+// product v = K~ w on the equispaced nodes (Sec. 2.2, Eq. equikereval2;
+// Sec. 2.4), done as a circular convolution on an L^s torus, L >= 2n, with a
+// hand-written shared-memory FFT (mixed-radix 2/3/4/5 Stockham, FP32,
+// twiddles rounded from FP64).
+//
+// The s+1 charge grids w (charges 1, y(1)-c, .., y(s)-c) are convolved with
+// K1 = (1+r^2)^-1 and K2 = K1^2 sampled at the node offsets, giving the s+2
+// node potentials of the Appendix:
+//   h1 = K1 * w_1,  h_{m+1} = K2 * w_{y(m)},  h_{s+2} = K2 * w_1.
+// Real signals are packed in pairs into complex transforms:
+//   C0 = w_1 + i w_{y1}, C1 = w_{y2} (+ i 0), CK = K1 + i K2.
+// K1 and K2 are even in every offset, so their spectra are real and even and
+// come out of one transform as Re / Im. The inverse transforms pack the
+// real results the same way: D0 = V1 + i V2 -> (h1, h2), D1 = V3 + i V4 ->
+// (h3, h_{s+2}).
+//
+// 2-D passes (one CTA per work item, grid-stride):
+//   rows_fwd_kernel  FFT along dimension 2 of the n rows of C0, C1 and of the
+//                    n distinct kernel rows (|offset| < n)
+//   cols_kernel      per column pair (k2, L-k2): FFT along dimension 1,
+//                    split the packed spectra, multiply by the kernel
+//                    spectra, pack, inverse FFT along dimension 1
+//   rows_inv_kernel  inverse FFT of the n needed rows, write the node
+//                    potentials, and the FP64 partial sums of Z = w_1 . h1 - N
+// 1-D: conv1d_kernel does the whole convolution in one CTA.
+#include <math.h>
+
+#include <algorithm>
+
+#include "fitsne_internal.cuh"
+
+namespace fitsne {
+
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// a * (s i)
+__device__ __forceinline__ float2 mul_si(float2 a, float s) { return make_float2(-s * a.y, s * a.x); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// R-point DFT in registers, X_k = sum_j x_j exp(s 2 pi i jk / R), s = -1 forward.
+template <int R>
+struct Dft;
+
+template <>
+struct Dft<2> {
+    __device__ __forceinline__ static void run(float2 (&v)[2], float) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <>
+struct Dft<3> {
+    __device__ __forceinline__ static void run(float2 (&v)[3], float s) {
+        const float h = 0.866025403784438647f;  // sqrt(3)/2
+        float2 t = cadd(v[1], v[2]);
+        float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+        float2 d = mul_si(csub(v[1], v[2]), s * h);
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, d);
+        v[2] = csub(m, d);
+    }
+};
+
+template <>
+struct Dft<4> {
+    __device__ __forceinline__ static void run(float2 (&v)[4], float s) {
+        float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        float2 t2 = cadd(v[1], v[3]), t3 = mul_si(csub(v[1], v[3]), s);
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+
+template <>
+struct Dft<5> {
+    __device__ __forceinline__ static void run(float2 (&v)[5], float s) {
+        const float c1 = 0.309016994374947424f;   // cos(2 pi / 5)
+        const float c2 = -0.809016994374947424f;  // cos(4 pi / 5)
+        const float s1 = 0.951056516295153572f;   // sin(2 pi / 5)
+        const float s2 = 0.587785252292473129f;   // sin(4 pi / 5)
+        float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+        float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+        float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+        float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+        float2 b1 = mul_si(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y), s);
+        float2 b2 = mul_si(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y), s);
+        v[0] = cadd(v[0], cadd(t1, t2));
+        v[1] = cadd(a1, b1);
+        v[4] = csub(a1, b1);
+        v[2] = cadd(a2, b2);
+        v[3] = csub(a2, b2);
+    }
+};
+
+// One Stockham stage of radix R for B transforms of length L stored
+// contiguously (x + b L -> y + b L); Ns = product of the earlier radices.
+template <int R>
+__device__ __forceinline__ void stage(const float2* __restrict__ x, float2* __restrict__ y, int L,
+                                      int Ns, int B, const float2* __restrict__ tw, float s) {
+    const int M = L / R;
+    const int stride = L / (Ns * R);
+    const int total = B * M;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int bi = t / M;
+        const int j = t - bi * M;
+        const float2* xb = x + bi * L;
+        float2* yb = y + bi * L;
+        const int k = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = xb[j + q * M];
+        if (Ns > 1) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                float2 w = __ldg(&tw[q * k * stride]);
+                if (s > 0.0f) w.y = -w.y;
+                v[q] = cmul(v[q], w);
+            }
+        }
+        Dft<R>::run(v, s);
+        const int out = (j - k) * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) yb[out + q * Ns] = v[q];
+    }
+}
+
+// B in-shared-memory FFTs of length e.L, ping-ponging between x and y.
+// Callers synchronise before; returns the buffer holding the result.
+__device__ float2* fft_batch(float2* x, float2* y, const FftEntry& e, int B,
+                             const float2* __restrict__ tw, float s) {
+    int Ns = 1;
+    for (int st = 0; st < e.nst; ++st) {
+        const int R = e.radix[st];
+        switch (R) {
+            case 2: stage<2>(x, y, e.L, Ns, B, tw, s); break;
+            case 3: stage<3>(x, y, e.L, Ns, B, tw, s); break;
+            case 4: stage<4>(x, y, e.L, Ns, B, tw, s); break;
+            default: stage<5>(x, y, e.L, Ns, B, tw, s); break;
+        }
+        __syncthreads();
+        float2* t = x;
+        x = y;
+        y = t;
+        Ns *= R;
+    }
+    return x;
+}
+
+// Kernel pair (K1, K2) at squared node distance d2 (in units of delta^2).
+__device__ __forceinline__ float2 kernel_pair(float delta2, int d2) {
+    const float k1 = __frcp_rn(1.0f + delta2 * (float)d2);
+    return make_float2(k1, k1 * k1);
+}
+
+// Signed node offset represented by circulant index i (|offset| < n), or -1
+// for the gap that outputs in [0, n) never reach.
+__device__ __forceinline__ int circ_offset(int i, int n, int L) {
+    return i < n ? i : (i > L - n ? L - i : -1);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// 2-D, pass 1: row FFTs. Work item m < 3n: type m / n (0: C0, 1: C1, 2: CK),
+// row m % n. Output rows of length L, row-major, at spec + type n L.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+rows_fwd_kernel(const float* __restrict__ w, const Params* __restrict__ params,
+                const FftEntry* __restrict__ table, const float2* __restrict__ tw_all,
+                float2* __restrict__ spec) {
+    extern __shared__ float2 sm[];
+    __shared__ FftEntry e;
+    const Params P = *params;
+    if (P.error) return;
+    if (threadIdx.x == 0) e = table[P.fft_idx];
+    __syncthreads();
+    const int n = P.n, L = P.L;
+    const int64_t G = (int64_t)n * n;
+    const float2* tw = tw_all + e.tw_off;
+    float2* A = sm;
+    float2* B = sm + L;
+    for (int m = blockIdx.x; m < 3 * n; m += gridDim.x) {
+        const int type = m / n, r = m - type * n;
+        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+            float2 v = make_float2(0.0f, 0.0f);
+            if (type == 0) {
+                if (c < n) v = make_float2(w[(int64_t)r * n + c], w[G + (int64_t)r * n + c]);
+            } else if (type == 1) {
+                if (c < n) v = make_float2(w[2 * G + (int64_t)r * n + c], 0.0f);
+            } else {
+                const int o = circ_offset(c, n, L);
+                if (o >= 0) v = kernel_pair(P.delta2, r * r + o * o);
+            }
+            A[c] = v;
+        }
+        __syncthreads();
+        const float2* res = fft_batch(A, B, e, 1, tw, -1.0f);
+        float2* dst = spec + (int64_t)type * n * L + (int64_t)r * L;
+        for (int c = threadIdx.x; c < L; c += blockDim.x) dst[c] = res[c];
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// 2-D, pass 2: column pairs (k2, L - k2), k2 = 0 .. L/2. Forward FFT of the
+// five columns, spectra products, inverse FFT of the four packed results,
+// which overwrite the first n rows of columns k2 and L - k2 of C0 and C1.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(512)
+cols_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ table,
+            const float2* __restrict__ tw_all, float2* __restrict__ spec) {
+    extern __shared__ float2 sm[];
+    __shared__ FftEntry e;
+    const Params P = *params;
+    if (P.error) return;
+    if (threadIdx.x == 0) e = table[P.fft_idx];
+    __syncthreads();
+    const int n = P.n, L = P.L;
+    const float2* tw = tw_all + e.tw_off;
+    float2* C0 = spec;
+    float2* C1 = spec + (int64_t)n * L;
+    const float2* CK = spec + 2 * (int64_t)n * L;
+    float2* X = sm;
+    float2* Yb = sm + 5 * L;
+    for (int k2 = blockIdx.x; k2 <= L / 2; k2 += gridDim.x) {
+        const int k2b = (L - k2) % L;
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            const bool in = i < n;
+            const float2 z = make_float2(0.0f, 0.0f);
+            X[i] = in ? C0[(int64_t)i * L + k2] : z;
+            X[L + i] = in ? C0[(int64_t)i * L + k2b] : z;
+            X[2 * L + i] = in ? C1[(int64_t)i * L + k2] : z;
+            X[3 * L + i] = in ? C1[(int64_t)i * L + k2b] : z;
+            const int o = circ_offset(i, n, L);
+            X[4 * L + i] = o >= 0 ? CK[(int64_t)o * L + k2] : z;
+        }
+        __syncthreads();
+        float2* F = fft_batch(X, Yb, e, 5, tw, -1.0f);
+        float2* O = (F == X) ? Yb : X;
+        for (int k1 = threadIdx.x; k1 < L; k1 += blockDim.x) {
+            const int k1n = (L - k1) % L;
+            const float2 xa = F[k1], xb = F[L + k1];
+            const float2 xa_m = F[k1n], xb_m = F[L + k1n];
+            // unpack C0 = w_1 + i w_{y1} at (k1, k2) and (k1, L - k2)
+            const float2 w1a = cscale(cadd(xa, conjf2(xb_m)), 0.5f);
+            const float2 dya = csub(xa, conjf2(xb_m));
+            const float2 wya = make_float2(0.5f * dya.y, -0.5f * dya.x);
+            const float2 w1b = cscale(cadd(xb, conjf2(xa_m)), 0.5f);
+            const float2 dyb = csub(xb, conjf2(xa_m));
+            const float2 wyb = make_float2(0.5f * dyb.y, -0.5f * dyb.x);
+            const float2 w2a = F[2 * L + k1], w2b = F[3 * L + k1];
+            const float2 ck = F[4 * L + k1];  // (K1^, K2^), equal at L - k2
+            const float K1 = ck.x, K2 = ck.y;
+            O[k1] = cadd(cscale(w1a, K1), mul_si(cscale(wya, K2), 1.0f));
+            O[L + k1] = cadd(cscale(w1b, K1), mul_si(cscale(wyb, K2), 1.0f));
+            O[2 * L + k1] = cadd(cscale(w2a, K2), mul_si(cscale(w1a, K2), 1.0f));
+            O[3 * L + k1] = cadd(cscale(w2b, K2), mul_si(cscale(w1b, K2), 1.0f));
+        }
+        __syncthreads();
+        const float2* R = fft_batch(O, F, e, 4, tw, 1.0f);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            C0[(int64_t)i * L + k2] = R[i];
+            C1[(int64_t)i * L + k2] = R[2 * L + i];
+            if (k2b != k2) {
+                C0[(int64_t)i * L + k2b] = R[L + i];
+                C1[(int64_t)i * L + k2b] = R[3 * L + i];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Block sum of one double per thread (blockDim.x <= 1024); result in thread 0.
+__device__ __forceinline__ double block_sum_d(double v, double* sred) {
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    __syncthreads();
+    if (lane == 0) sred[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += sred[k];
+    return t;
+}
+
+// Last block of a grid: sums the per-row partials in row order and publishes
+// Z = sum_i h1(y_i) - N = w_1 . h1 - N (the two agree: both equal the sum of
+// L_g(y_i) v1[g] over points and nodes).
+__device__ void publish_Z(const double* __restrict__ z_partial, int rows, Params* params,
+                          double* Z_out, int64_t N) {
+    double S = 0.0;
+    for (int r = 0; r < rows; ++r) S += __ldcg(&z_partial[r]);
+    const double Z = S - (double)N;
+    params->Z = Z;
+    params->inv_Z = (float)(1.0 / Z);
+    if (Z_out) *Z_out = Z;
+}
+
+// ----------------------------------------------------------------------------
+// 2-D, pass 3: inverse row FFTs of the first n rows of D0 and D1; node
+// potentials (h1, h2, h3, h4) / L^2 for columns < n; FP64 row sums of w_1 h1.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+rows_inv_kernel(const float* __restrict__ w, Params* params, const FftEntry* __restrict__ table,
+                const float2* __restrict__ tw_all, const float2* __restrict__ spec,
+                float4* __restrict__ hgrid, double* __restrict__ z_partial,
+                unsigned* __restrict__ ticket, double* Z_out, int64_t N) {
+    extern __shared__ float2 sm[];
+    __shared__ FftEntry e;
+    __shared__ double sred[32];
+    __shared__ bool s_last;
+    const Params P = *params;
+    const int n = P.n, L = P.L;
+    if (!P.error) {
+        if (threadIdx.x == 0) e = table[P.fft_idx];
+        __syncthreads();
+        const float2* tw = tw_all + e.tw_off;
+        const float2* D0 = spec;
+        const float2* D1 = spec + (int64_t)n * L;
+        float2* X = sm;
+        float2* Yb = sm + 2 * L;
+        const float scale = 1.0f / ((float)L * (float)L);
+        for (int r = blockIdx.x; r < n; r += gridDim.x) {
+            for (int c = threadIdx.x; c < L; c += blockDim.x) {
+                X[c] = D0[(int64_t)r * L + c];
+                X[L + c] = D1[(int64_t)r * L + c];
+            }
+            __syncthreads();
+            const float2* R = fft_batch(X, Yb, e, 2, tw, 1.0f);
+            double zp = 0.0;
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                const float2 a = R[c], b = R[L + c];
+                const float4 h = make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
+                hgrid[(int64_t)r * n + c] = h;
+                zp += (double)w[(int64_t)r * n + c] * (double)h.x;
+            }
+            const double t = block_sum_d(zp, sred);
+            if (threadIdx.x == 0) z_partial[r] = t;
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    *ticket = 0u;
+    if (!P.error) publish_Z(z_partial, n, params, Z_out, N);
+}
+
+// ----------------------------------------------------------------------------
+// 1-D: the whole convolution in one CTA. C0 = w_1 + i w_y and CK = K1 + i K2
+// forward; D0 = W1 K1^ + i Wy K2^ and D1 = W1 K2^ inverse; node potentials
+// (h1, h2, 0, h3) / L; Z = w_1 . h1 - N in FP64.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+conv1d_kernel(const float* __restrict__ w, Params* params, const FftEntry* __restrict__ table,
+              const float2* __restrict__ tw_all, float4* __restrict__ hgrid, double* Z_out,
+              int64_t N) {
+    extern __shared__ float2 sm[];
+    __shared__ FftEntry e;
+    __shared__ double sred[32];
+    const Params P = *params;
+    if (P.error) return;
+    if (threadIdx.x == 0) e = table[P.fft_idx];
+    __syncthreads();
+    const int n = P.n, L = P.L;
+    const float2* tw = tw_all + e.tw_off;
+    float2* X = sm;
+    float2* Yb = sm + 2 * L;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        X[i] = i < n ? make_float2(w[i], w[n + i]) : make_float2(0.0f, 0.0f);
+        const int o = circ_offset(i, n, L);
+        X[L + i] = o >= 0 ? kernel_pair(P.delta2, o * o) : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    float2* F = fft_batch(X, Yb, e, 2, tw, -1.0f);
+    float2* O = (F == X) ? Yb : X;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        const int kn = (L - k) % L;
+        const float2 x = F[k], xm = conjf2(F[kn]);
+        const float2 w1 = cscale(cadd(x, xm), 0.5f);
+        const float2 d = csub(x, xm);
+        const float2 wy = make_float2(0.5f * d.y, -0.5f * d.x);
+        const float2 ck = F[L + k];
+        O[k] = cadd(cscale(w1, ck.x), mul_si(cscale(wy, ck.y), 1.0f));
+        O[L + k] = cscale(w1, ck.y);
+    }
+    __syncthreads();
+    const float2* R = fft_batch(O, F, e, 2, tw, 1.0f);
+    const float scale = 1.0f / (float)L;
+    double zp = 0.0;
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+        const float4 h = make_float4(R[g].x * scale, R[g].y * scale, 0.0f, R[L + g].x * scale);
+        hgrid[g] = h;
+        zp += (double)w[g] * (double)h.x;
+    }
+    const double t = block_sum_d(zp, sred);
+    if (threadIdx.x == 0) {
+        const double Z = t - (double)N;
+        params->Z = Z;
+        params->inv_Z = (float)(1.0 / Z);
+        if (Z_out) *Z_out = Z;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Launch geometry depends only on the plan's capacities, so one enqueued
+// sequence serves every iteration whatever N_int the box rule picks.
+// ----------------------------------------------------------------------------
+static size_t smem_rows_fwd(const tsne_plan* pl) { return sizeof(float2) * 2 * pl->L_max; }
+static size_t smem_cols(const tsne_plan* pl) { return sizeof(float2) * 10 * pl->L_max; }
+static size_t smem_rows_inv(const tsne_plan* pl) { return sizeof(float2) * 4 * pl->L_max; }
+static size_t smem_1d(const tsne_plan* pl) { return sizeof(float2) * 4 * pl->L_max; }
+
+cudaError_t fft_configure(tsne_plan* pl) {
+    cudaError_t e = cudaSuccess;
+    if (pl->s == 2) {
+        e = cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_rows_fwd(pl));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_cols(pl));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_rows_inv(pl));
+    } else {
+        e = cudaFuncSetAttribute(conv1d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_1d(pl));
+    }
+    return e;
+}
+
+cudaError_t launch_convolution(tsne_plan* pl, double* Z_out) {
+    if (pl->s == 2) {
+        const int g1 = (int)std::min<int64_t>(3 * (int64_t)pl->n_max, 4 * pl->sm_count);
+        rows_fwd_kernel<<<g1, 256, smem_rows_fwd(pl), pl->stream>>>(pl->w, pl->params, pl->fft_table,
+                                                                     pl->twiddles, pl->spec);
+        const int g2 = (int)std::min<int64_t>(pl->L_max / 2 + 1, 2 * pl->sm_count);
+        cols_kernel<<<g2, 512, smem_cols(pl), pl->stream>>>(pl->params, pl->fft_table, pl->twiddles,
+                                                            pl->spec);
+        const int g3 = (int)std::min<int64_t>(pl->n_max, 4 * pl->sm_count);
+        rows_inv_kernel<<<g3, 256, smem_rows_inv(pl), pl->stream>>>(
+            pl->w, pl->params, pl->fft_table, pl->twiddles, pl->spec, pl->hgrid, pl->z_partial,
+            pl->tickets + 2, Z_out, pl->N);
+        pl->launches += 3;
+    } else {
+        conv1d_kernel<<<1, 1024, smem_1d(pl), pl->stream>>>(pl->w, pl->params, pl->fft_table,
+                                                            pl->twiddles, pl->hgrid, Z_out, pl->N);
+        pl->launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fitsne

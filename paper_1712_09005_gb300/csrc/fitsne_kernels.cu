@@ -1,0 +1,809 @@
+// Per-point and per-entry kernels of the FIt-SNE gradient on sm_103a:
+//   box_kernel      bounding box and interval rule (Sec. 2.2, 2.4, 2.5)
+//   count/scatter   counting sort of the points by box (the "points in I_l"
+//                   loops of Algorithm 1)
+//   scan kernels    box offsets and the spread work list
+//   spread_kernel   Step 1: w_m = sum_{y_i in I_l} L_m(y_i) q_i per box
+//   force_kernel    attraction over the CSR rows (Sec. 3) fused with Step 3
+//                   (interpolate back), the Appendix assembly of F_rep and,
+//                   for a descent step, the gains/momentum update
+//   kl_kernel       KL(P || Q) of Sec. 1.1 with FP64 sums
+// None of these kernels uses global floating-point atomics except the spread
+// of boxes holding more than one chunk of points.
+#include <math.h>
+
+#include "fitsne_internal.cuh"
+
+namespace fitsne {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Reduces a[0..NV) (NV a multiple of 32) across the warp so that, for every
+// group g of 32 values, lane l ends with the warp total of value g*32 + l in
+// a[g*32]. 31 shuffles per group instead of 5 per value.
+template <int NV>
+__device__ __forceinline__ void warp_transpose_reduce(float (&a)[NV], int lane) {
+#pragma unroll
+    for (int g = 0; g < NV / 32; ++g) {
+        float* v = a + g * 32;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const bool upper = (lane & off) != 0;
+#pragma unroll
+            for (int i = 0; i < off; ++i) {
+                float send = upper ? v[i] : v[i + off];
+                float keep = upper ? v[i + off] : v[i];
+                v[i] = keep + __shfl_xor_sync(kFull, send, off);
+            }
+        }
+    }
+}
+
+template <int S>
+__device__ __forceinline__ int box_of(const float* __restrict__ Y, int64_t i, const Params& P) {
+    if (S == 2) {
+        float2 y = reinterpret_cast<const float2*>(Y)[i];
+        return interval_of(y.x, P) * P.n_int + interval_of(y.y, P);
+    } else {
+        return interval_of(Y[i], P);
+    }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// Bounding box: per-block min/max, then the last block to finish derives the
+// box, N_int, node spacing and FFT length (Sec. 2.2, 2.4, 2.5). The FP32
+// rule matches the oracle's bit for bit.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBoxThreads)
+box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_fixed, int n_min,
+           int n_int_max, int force, float f_y_min, float f_width, int f_n_int,
+           float* __restrict__ partial, unsigned* __restrict__ ticket, Params* __restrict__ params,
+           const FftEntry* __restrict__ table, int n_fft) {
+    float lo = INFINITY, hi = -INFINITY;
+    int bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
+        const int64_t n4 = count / 4;
+        const float4* Y4 = reinterpret_cast<const float4*>(Y);
+        for (int64_t k = k0; k < n4; k += stride) {
+            float4 v = __ldg(&Y4[k]);
+            bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
+            lo = fminf(lo, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
+            hi = fmaxf(hi, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+        }
+        for (int64_t k = n4 * 4 + k0; k < count; k += stride) {
+            float v = Y[k];
+            bad |= !isfinite(v);
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
+    } else {
+        for (int64_t k = k0; k < count; k += stride) {
+            float v = Y[k];
+            bad |= !isfinite(v);
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+    }
+    __shared__ float s_lo[kBoxThreads / 32], s_hi[kBoxThreads / 32];
+    __shared__ bool s_last;
+    bad = __syncthreads_or(bad);
+    const int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < kBoxThreads / 32; ++i) { lo = fminf(lo, s_lo[i]); hi = fmaxf(hi, s_hi[i]); }
+        partial[2 * blockIdx.x] = bad ? NAN : lo;
+        partial[2 * blockIdx.x + 1] = hi;
+        __threadfence();
+        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    bool any_bad = false;
+    lo = INFINITY;
+    hi = -INFINITY;
+    for (unsigned i = 0; i < gridDim.x; ++i) {
+        float a = __ldcg(&partial[2 * i]), b = __ldcg(&partial[2 * i + 1]);
+        if (isnan(a)) any_bad = true;
+        lo = fminf(lo, a);
+        hi = fmaxf(hi, b);
+    }
+    *ticket = 0u;
+    Params P;
+    P.error = __ldcg(&params->error);
+    if (any_bad) { P.error = TSNE_ERR_NONFINITE; lo = 0.0f; hi = 1.0f; }
+    float y_min, width;
+    int n_int;
+    if (force) {
+        y_min = f_y_min;
+        width = f_width;
+        n_int = f_n_int;
+    } else {
+        y_min = lo;
+        width = __fsub_rn(hi, lo);
+        if (!(width > 0.0f)) width = 1.0f;
+        if (n_int_fixed > 0) {
+            n_int = n_int_fixed;
+        } else {
+            float c = ceilf(width);
+            if (c > (float)n_int_max) c = (float)n_int_max;
+            n_int = (int)c;
+            if (n_int < n_min) n_int = n_min;
+            if (n_int > n_int_max) n_int = n_int_max;
+        }
+    }
+    P.y_min = y_min;
+    P.width = width;
+    P.n_int = n_int;
+    P.b = __fdiv_rn(width, (float)n_int);
+    P.inv_b = __fdiv_rn(1.0f, P.b);
+    P.delta = __fdiv_rn(P.b, (float)p);
+    P.inv_delta = __fdiv_rn((float)p, P.b);
+    P.delta2 = __fmul_rn(P.delta, P.delta);
+    P.centre = __fadd_rn(y_min, __fmul_rn(0.5f, width));
+    P.n = p * n_int;
+    P.n_boxes = (s == 2) ? n_int * n_int : n_int;
+    int idx = n_fft - 1;
+    for (int i = 0; i < n_fft; ++i) {
+        if (table[i].L >= 2 * P.n) { idx = i; break; }
+    }
+    P.fft_idx = idx;
+    P.L = table[idx].L;
+    P.n_chunks = 0;
+    P.pad = 0;
+    P.Z = 0.0;
+    P.inv_Z = 0.0f;
+    P.pad2 = 0.0f;
+    *params = P;
+}
+
+// ----------------------------------------------------------------------------
+// Counting sort by box: histogram (warp-aggregated integer atomics), scan,
+// scatter. Points of one box end up contiguous in sorted_y; their order
+// within the box is not fixed, which only permutes the spread's FP32 sums.
+// ----------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(256)
+count_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ params,
+             int32_t* __restrict__ counts) {
+    const Params P = *params;
+    if (P.error) return;
+    const int lane = threadIdx.x % 32;
+    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < N;
+         base += nwarp * 32) {
+        const int64_t i = base + lane;
+        const int box = (i < N) ? box_of<S>(Y, i, P) : -1;
+        const unsigned peers = __match_any_sync(kFull, box);
+        const int leader = __ffs(peers) - 1;
+        if (box >= 0 && lane == leader) atomicAdd(&counts[box], __popc(peers));
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256)
+scatter_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ params,
+               int32_t* __restrict__ cursor, float* __restrict__ sorted_y) {
+    const Params P = *params;
+    if (P.error) return;
+    const int lane = threadIdx.x % 32;
+    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < N;
+         base += nwarp * 32) {
+        const int64_t i = base + lane;
+        const int box = (i < N) ? box_of<S>(Y, i, P) : -1;
+        const unsigned peers = __match_any_sync(kFull, box);
+        const int leader = __ffs(peers) - 1;
+        int pos = 0;
+        if (box >= 0 && lane == leader) pos = atomicAdd(&cursor[box], __popc(peers));
+        pos = __shfl_sync(kFull, pos, leader) + __popc(peers & lt);
+        if (box >= 0) {
+            if (S == 2)
+                reinterpret_cast<float2*>(sorted_y)[pos] = reinterpret_cast<const float2*>(Y)[i];
+            else
+                sorted_y[pos] = Y[i];
+        }
+    }
+}
+
+// Block-wide exclusive scan of one int per thread (1024 threads).
+__device__ __forceinline__ int block_exclusive_scan(int v, int* smem_warp, int& total) {
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = (lane < (int)(blockDim.x / 32)) ? smem_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        smem_warp[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    total = smem_warp[blockDim.x / 32 - 1];
+    int excl = x - v + (wid > 0 ? smem_warp[wid - 1] : 0);
+    __syncthreads();
+    return excl;
+}
+
+// Pass 1: per-block totals of points and of spread chunks (ceil(count/kChunk));
+// the last block turns them into exclusive block offsets.
+__global__ void __launch_bounds__(1024)
+scan_blocks_kernel(const int32_t* __restrict__ counts, Params* params,
+                   int32_t* __restrict__ block_pts, int32_t* __restrict__ block_chunks,
+                   unsigned* __restrict__ ticket) {
+    __shared__ int sw[32];
+    __shared__ bool s_last;
+    const int nb = params->n_boxes;
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * 2;
+    int c0 = base < nb ? counts[base] : 0;
+    int c1 = base + 1 < nb ? counts[base + 1] : 0;
+    int pts = c0 + c1;
+    int chk = (c0 + kChunk - 1) / kChunk + (c1 + kChunk - 1) / kChunk;
+    int tp, tc;
+    block_exclusive_scan(pts, sw, tp);
+    block_exclusive_scan(chk, sw, tc);
+    if (threadIdx.x == 0) {
+        block_pts[blockIdx.x] = tp;
+        block_chunks[blockIdx.x] = tc;
+        __threadfence();
+        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    int carry_p = 0, carry_c = 0;
+    for (unsigned start = 0; start < gridDim.x; start += blockDim.x) {
+        const unsigned i = start + threadIdx.x;
+        int vp = i < gridDim.x ? __ldcg(&block_pts[i]) : 0;
+        int vc = i < gridDim.x ? __ldcg(&block_chunks[i]) : 0;
+        int sp, sc;
+        int ep = block_exclusive_scan(vp, sw, sp);
+        int ec = block_exclusive_scan(vc, sw, sc);
+        if (i < gridDim.x) {
+            block_pts[i] = carry_p + ep;
+            block_chunks[i] = carry_c + ec;
+        }
+        carry_p += sp;
+        carry_c += sc;
+    }
+    if (threadIdx.x == 0) {
+        params->n_chunks = carry_c;
+        *ticket = 0u;
+    }
+}
+
+// Pass 2: box offsets, scatter cursors, chunk -> box table; resets the counts
+// and zeroes each box's nodes in the spread grids.
+template <int S, int PP>
+__global__ void __launch_bounds__(1024)
+scan_boxes_kernel(int32_t* __restrict__ counts, const Params* __restrict__ params,
+                  const int32_t* __restrict__ block_pts, const int32_t* __restrict__ block_chunks,
+                  int32_t* __restrict__ box_start, int32_t* __restrict__ cursor,
+                  int32_t* __restrict__ chunk_start, int32_t* __restrict__ chunk_box,
+                  float* __restrict__ w, int64_t N) {
+    __shared__ int sw[32];
+    const Params P = *params;
+    const int nb = P.n_boxes;
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * 2;
+    int c[2] = {base < nb ? counts[base] : 0, base + 1 < nb ? counts[base + 1] : 0};
+    int k[2] = {(c[0] + kChunk - 1) / kChunk, (c[1] + kChunk - 1) / kChunk};
+    int tp, tc;
+    int ep = block_exclusive_scan(c[0] + c[1], sw, tp) + block_pts[blockIdx.x];
+    int ec = block_exclusive_scan(k[0] + k[1], sw, tc) + block_chunks[blockIdx.x];
+    const int n = P.n;
+    const int64_t G = (S == 2) ? (int64_t)n * n : n;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int b = base + u;
+        if (b < nb) {
+            box_start[b] = ep;
+            cursor[b] = ep;
+            chunk_start[b] = ec;
+            counts[b] = 0;
+            for (int q = 0; q < k[u]; ++q) chunk_box[ec + q] = b;
+            const int bx = (S == 2) ? b / P.n_int : b;
+            const int by = (S == 2) ? b % P.n_int : 0;
+            for (int ch = 0; ch <= S; ++ch)
+                for (int j1 = 0; j1 < PP; ++j1)
+                    for (int j2 = 0; j2 < (S == 2 ? PP : 1); ++j2) {
+                        int64_t g = (S == 2) ? (int64_t)(bx * PP + j1) * n + (by * PP + j2)
+                                             : (int64_t)(bx * PP + j1);
+                        w[ch * G + g] = 0.0f;
+                    }
+            if (b == nb - 1) {
+                box_start[nb] = (int32_t)N;
+                chunk_start[nb] = ec + k[u];
+            }
+        }
+        ep += c[u];
+        ec += k[u];
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Step 1 (spread): one warp per chunk of at most kChunk points of one box.
+// Each lane accumulates the (s+1) p^s node sums of its points in registers
+// (charges 1 and y(m) - centre); a transpose reduction gives lane v the warp
+// total of value v. Boxes with one chunk store; larger boxes add atomically.
+// ----------------------------------------------------------------------------
+template <int S, int PP>
+__global__ void __launch_bounds__(256)
+spread_kernel(const float* __restrict__ sorted_y, const int32_t* __restrict__ box_start,
+              const int32_t* __restrict__ chunk_start, const int32_t* __restrict__ chunk_box,
+              const Params* __restrict__ params, float* __restrict__ w) {
+    constexpr int NODES = (S == 2) ? PP * PP : PP;
+    constexpr int NVAL = (S + 1) * NODES;
+    constexpr int NV = (NVAL + 31) / 32 * 32;
+    const Params P = *params;
+    if (P.error) return;
+    const int lane = threadIdx.x % 32;
+    const int nwarp = gridDim.x * blockDim.x / 32;
+    const int n = P.n;
+    const int64_t G = (S == 2) ? (int64_t)n * n : n;
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) / 32; q < P.n_chunks; q += nwarp) {
+        const int box = chunk_box[q];
+        const int bs = box_start[box];
+        const int cnt = box_start[box + 1] - bs;
+        const int ci = q - chunk_start[box];
+        const int start = bs + ci * kChunk;
+        const int len = min(kChunk, cnt - ci * kChunk);
+        const int bx = (S == 2) ? box / P.n_int : box;
+        const int by = (S == 2) ? box % P.n_int : 0;
+        float acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = 0.0f;
+        for (int k = lane; k < len; k += 32) {
+            float L1[PP], L2[PP];
+            float q1, q2 = 0.0f;
+            if (S == 2) {
+                float2 y = reinterpret_cast<const float2*>(sorted_y)[start + k];
+                lagrange<PP>(local_t(y.x, bx, P), L1);
+                lagrange<PP>(local_t(y.y, by, P), L2);
+                q1 = y.x - P.centre;
+                q2 = y.y - P.centre;
+            } else {
+                float y = sorted_y[start + k];
+                lagrange<PP>(local_t(y, bx, P), L1);
+                q1 = y - P.centre;
+            }
+#pragma unroll
+            for (int j1 = 0; j1 < PP; ++j1) {
+#pragma unroll
+                for (int j2 = 0; j2 < (S == 2 ? PP : 1); ++j2) {
+                    const float wt = (S == 2) ? L1[j1] * L2[j2] : L1[j1];
+                    const int node = (S == 2) ? j1 * PP + j2 : j1;
+                    acc[node] += wt;
+                    acc[NODES + node] += wt * q1;
+                    if (S == 2) acc[2 * NODES + node] += wt * q2;
+                }
+            }
+        }
+        warp_transpose_reduce<NV>(acc, lane);
+        const bool multi = cnt > kChunk;
+#pragma unroll
+        for (int g = 0; g < NV / 32; ++g) {
+            const int v = g * 32 + lane;
+            if (v < NVAL) {
+                const int ch = v / NODES, node = v % NODES;
+                const int j1 = (S == 2) ? node / PP : node;
+                const int j2 = (S == 2) ? node % PP : 0;
+                const int64_t gi = (S == 2) ? (int64_t)(bx * PP + j1) * n + (by * PP + j2)
+                                            : (int64_t)(bx * PP + j1);
+                float* dst = &w[ch * G + gi];
+                if (multi) atomicAdd(dst, acc[g * 32]);
+                else *dst = acc[g * 32];
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Attraction + Step 3 + gradient (+ update). One warp per CSR row i:
+//   A_i = sum_j p_ij (y_i - y_j) / (1 + |y_i - y_j|^2)                 (Sec. 3)
+//   h_k(y_i) = sum over the p^s nodes of y_i's box of L(y_i) v_k[node] (Step 3)
+//   F_rep,i(m) = (h_{m+1} - (y_i(m) - c) h_{s+2}) / Z                  (Appendix)
+//   dY_i = 4 (alpha A_i + F_rep,i)                                     (Sec. 1.2)
+// The h values carry the centred charges y - c, so y_i(m) - c multiplies
+// h_{s+2}; its rounding error is carried along exactly (two-sum).
+// ----------------------------------------------------------------------------
+struct StepArgs {
+    float* Y_new;
+    float* uY;
+    float* gains;
+    float momentum, lr, min_gain, gain_inc, gain_dec;
+};
+
+__device__ __forceinline__ float update_one(float y, float dy, float& u, float& g,
+                                            const StepArgs& a) {
+    const int sd = (dy > 0.0f) - (dy < 0.0f);
+    const int su = (u > 0.0f) - (u < 0.0f);
+    float gn = (sd != su) ? g + a.gain_inc : g * a.gain_dec;
+    gn = fmaxf(gn, a.min_gain);
+    g = gn;
+    u = a.momentum * u - a.lr * gn * dy;
+    return y + u;
+}
+
+template <int S, int PP, bool STEP>
+__global__ void __launch_bounds__(256)
+force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+             const float* __restrict__ val, const float* __restrict__ Y,
+             const Params* __restrict__ params, const float4* __restrict__ hgrid, float alpha,
+             float* __restrict__ dY, StepArgs sa, int64_t N) {
+    constexpr int NODES = (S == 2) ? PP * PP : PP;
+    const Params P = *params;
+    if (P.error) return;
+    const int lane = threadIdx.x % 32;
+    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
+    const float invZ = P.inv_Z;
+    const int n = P.n;
+    // this lane's node of the p^s nodes of a box
+    const int j1 = (S == 2) ? lane / PP : lane;
+    const int j2 = (S == 2) ? lane % PP : 0;
+    const bool node_lane = lane < NODES;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; i < N; i += nwarp) {
+        float yi0, yi1 = 0.0f;
+        if (S == 2) {
+            float2 t = reinterpret_cast<const float2*>(Y)[i];
+            yi0 = t.x;
+            yi1 = t.y;
+        } else {
+            yi0 = Y[i];
+        }
+        const int beg = row_ptr[i], end = row_ptr[i + 1];
+        float a0 = 0.0f, a1 = 0.0f;
+        int e = beg + lane;
+        // four independent gathers in flight per lane
+        for (; e + 96 < end; e += 128) {
+            int jj[4];
+            float vv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { jj[u] = __ldcs(&col[e + 32 * u]); vv[u] = __ldcs(&val[e + 32 * u]); }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (S == 2) {
+                    float2 yj = __ldg(reinterpret_cast<const float2*>(Y) + jj[u]);
+                    float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
+                    float q = vv[u] * __frcp_rn(1.0f + d0 * d0 + d1 * d1);
+                    a0 += q * d0;
+                    a1 += q * d1;
+                } else {
+                    float d0 = yi0 - __ldg(Y + jj[u]);
+                    float q = vv[u] * __frcp_rn(1.0f + d0 * d0);
+                    a0 += q * d0;
+                }
+            }
+        }
+        for (; e < end; e += 32) {
+            int j = __ldcs(&col[e]);
+            float v = __ldcs(&val[e]);
+            if (S == 2) {
+                float2 yj = __ldg(reinterpret_cast<const float2*>(Y) + j);
+                float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
+                float q = v * __frcp_rn(1.0f + d0 * d0 + d1 * d1);
+                a0 += q * d0;
+                a1 += q * d1;
+            } else {
+                float d0 = yi0 - __ldg(Y + j);
+                float q = v * __frcp_rn(1.0f + d0 * d0);
+                a0 += q * d0;
+            }
+        }
+        a0 = warp_sum(a0);
+        if (S == 2) a1 = warp_sum(a1);
+
+        // Step 3: interpolate the node potentials of y_i's box
+        const int l1 = interval_of(yi0, P);
+        const int l2 = (S == 2) ? interval_of(yi1, P) : 0;
+        float r1 = 0.0f, r2 = 0.0f, r3 = 0.0f;
+        if (node_lane) {
+            float L1[PP];
+            lagrange<PP>(local_t(yi0, l1, P), L1);
+            float w1 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < PP; ++k) if (k == j1) w1 = L1[k];
+            float wt = w1;
+            int64_t gi;
+            if (S == 2) {
+                float L2[PP];
+                lagrange<PP>(local_t(yi1, l2, P), L2);
+                float w2 = 0.0f;
+#pragma unroll
+                for (int k = 0; k < PP; ++k) if (k == j2) w2 = L2[k];
+                wt = w1 * w2;
+                gi = (int64_t)(l1 * PP + j1) * n + (l2 * PP + j2);
+            } else {
+                gi = l1 * PP + j1;
+            }
+            const float4 h = __ldg(&hgrid[gi]);
+            r1 = wt * h.y;
+            r2 = wt * h.z;
+            r3 = wt * h.w;
+        }
+#pragma unroll
+        for (int o = (NODES > 16 ? 16 : (NODES > 8 ? 8 : (NODES > 4 ? 4 : (NODES > 2 ? 2 : 1))));
+             o >= 1; o >>= 1) {
+            r1 += __shfl_xor_sync(kFull, r1, o);
+            if (S == 2) r2 += __shfl_xor_sync(kFull, r2, o);
+            r3 += __shfl_xor_sync(kFull, r3, o);
+        }
+        if (lane == 0) {
+        // Appendix: F_rep(m) = (h_{m+1} - (y(m) - c) h_{s+2}) / Z
+        float c_hi = yi0 - P.centre;
+        float bb = c_hi - yi0;
+        float c_lo = (yi0 - (c_hi - bb)) + (-P.centre - bb);
+        const float f0 = (__fmaf_rn(-c_hi, r3, r1) - c_lo * r3) * invZ;
+        const float g0 = 4.0f * (alpha * a0 + f0);
+        float g1 = 0.0f;
+        if (S == 2) {
+            float d_hi = yi1 - P.centre;
+            float b2 = d_hi - yi1;
+            float d_lo = (yi1 - (d_hi - b2)) + (-P.centre - b2);
+            const float f1 = (__fmaf_rn(-d_hi, r3, r2) - d_lo * r3) * invZ;
+            g1 = 4.0f * (alpha * a1 + f1);
+        }
+        if (!STEP) {
+            if (S == 2) reinterpret_cast<float2*>(dY)[i] = make_float2(g0, g1);
+            else dY[i] = g0;
+        } else {
+            if (S == 2) {
+                float2 u = reinterpret_cast<float2*>(sa.uY)[i];
+                float2 g = reinterpret_cast<float2*>(sa.gains)[i];
+                float n0 = update_one(yi0, g0, u.x, g.x, sa);
+                float n1 = update_one(yi1, g1, u.y, g.y, sa);
+                reinterpret_cast<float2*>(sa.uY)[i] = u;
+                reinterpret_cast<float2*>(sa.gains)[i] = g;
+                reinterpret_cast<float2*>(sa.Y_new)[i] = make_float2(n0, n1);
+            } else {
+                float u = sa.uY[i], g = sa.gains[i];
+                float n0 = update_one(yi0, g0, u, g, sa);
+                sa.uY[i] = u;
+                sa.gains[i] = g;
+                sa.Y_new[i] = n0;
+            }
+        }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// KL(P || Q) = sum p log p + sum p log(1 + d^2) + (sum p) log Z over the stored
+// entries (Sec. 1.1). Per-entry logarithms in FP32, all sums in FP64, reduced
+// in a fixed order (per block, then by the last block).
+// ----------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(256)
+kl_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+          const float* __restrict__ val, const float* __restrict__ Y, int64_t N,
+          const Params* __restrict__ params, double* __restrict__ partial,
+          unsigned* __restrict__ ticket, double* __restrict__ out) {
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
+    double acc = 0.0, psum = 0.0;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; i < N; i += nwarp) {
+        float yi0, yi1 = 0.0f;
+        if (S == 2) {
+            float2 t = reinterpret_cast<const float2*>(Y)[i];
+            yi0 = t.x;
+            yi1 = t.y;
+        } else {
+            yi0 = Y[i];
+        }
+        for (int e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+            const float p = val[e];
+            if (!(p > 0.0f)) continue;
+            const int j = col[e];
+            float d2;
+            if (S == 2) {
+                float2 yj = reinterpret_cast<const float2*>(Y)[j];
+                float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
+                d2 = d0 * d0 + d1 * d1;
+            } else {
+                float d0 = yi0 - Y[j];
+                d2 = d0 * d0;
+            }
+            acc += (double)p * ((double)logf(p) + (double)log1pf(d2));
+            psum += (double)p;
+        }
+    }
+    acc = warp_sum_d(acc);
+    psum = warp_sum_d(psum);
+    __shared__ double s_a[8], s_p[8];
+    __shared__ bool s_last;
+    if (lane == 0) { s_a[wid] = acc; s_p[wid] = psum; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, ps = 0.0;
+        for (int k = 0; k < (int)(blockDim.x / 32); ++k) { a += s_a[k]; ps += s_p[k]; }
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = ps;
+        __threadfence();
+        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    double a = 0.0, ps = 0.0;
+    for (unsigned k = 0; k < gridDim.x; ++k) {
+        a += __ldcg(&partial[2 * k]);
+        ps += __ldcg(&partial[2 * k + 1]);
+    }
+    *ticket = 0u;
+    *out = a + ps * log(__ldcg(&params->Z));
+}
+
+// ----------------------------------------------------------------------------
+// CSR check: row_ptr[0] = 0, monotone, row_ptr[N] = nnz, 0 <= col < N,
+// col != row, 0 <= val < inf. Sets *flag to 1 on the first violation.
+// ----------------------------------------------------------------------------
+__global__ void validate_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const float* __restrict__ val, int64_t N, int64_t nnz,
+                                int32_t* __restrict__ flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const int64_t a = row_ptr[i], b = row_ptr[i + 1];
+        bool bad = (a > b) || (a < 0) || (b > nnz) || (i == 0 && a != 0) || (i == N - 1 && b != nnz);
+        if (!bad) {
+            for (int64_t e = a; e < b; ++e) {
+                const int64_t j = col[e];
+                const float v = val[e];
+                if (j < 0 || j >= N || j == i || !(v >= 0.0f) || isinf(v)) { bad = true; break; }
+            }
+        }
+        if (bad) atomicExch(flag, 1);
+    }
+}
+
+__global__ void fill_kernel(float* __restrict__ a, float v, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = v;
+}
+
+// ----------------------------------------------------------------------------
+// Launchers
+// ----------------------------------------------------------------------------
+static int grid_for(const tsne_plan* pl, int64_t items, int per_block, int per_sm) {
+    int64_t b = (items + per_block - 1) / per_block;
+    int64_t cap = (int64_t)pl->sm_count * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_box(tsne_plan* pl, const float* Y) {
+    box_kernel<<<kBoxBlocks, kBoxThreads, 0, pl->stream>>>(
+        Y, pl->N * pl->s, pl->s, pl->p, pl->n_int_fixed, pl->n_min, pl->n_int_max, pl->force_box,
+        pl->force_y_min, pl->force_width, pl->force_n_int, pl->box_partial, pl->tickets + 0,
+        pl->params, pl->fft_table, pl->n_fft);
+    pl->launches += 1;
+    return cudaGetLastError();
+}
+
+template <int S, int PP>
+static void sort_and_spread_impl(tsne_plan* pl, const float* Y) {
+    const int gp = grid_for(pl, pl->N, 256, 8);
+    count_kernel<S><<<gp, 256, 0, pl->stream>>>(Y, pl->N, pl->params, pl->counts);
+    scan_blocks_kernel<<<pl->scan_blocks, 1024, 0, pl->stream>>>(
+        pl->counts, pl->params, pl->block_pts, pl->block_chunks, pl->tickets + 1);
+    scan_boxes_kernel<S, PP><<<pl->scan_blocks, 1024, 0, pl->stream>>>(
+        pl->counts, pl->params, pl->block_pts, pl->block_chunks, pl->box_start, pl->cursor,
+        pl->chunk_start, pl->chunk_box, pl->w, pl->N);
+    scatter_kernel<S><<<gp, 256, 0, pl->stream>>>(Y, pl->N, pl->params, pl->cursor, pl->sorted_y);
+    const int gs = grid_for(pl, pl->chunk_cap * 32, 256, 8);
+    spread_kernel<S, PP><<<gs, 256, 0, pl->stream>>>(pl->sorted_y, pl->box_start, pl->chunk_start,
+                                                     pl->chunk_box, pl->params, pl->w);
+    pl->launches += 5;
+}
+
+#define FITSNE_DISPATCH(S_, FN, ...)                                   \
+    switch (pl->p) {                                                   \
+        case 2: FN<S_, 2>(__VA_ARGS__); break;                         \
+        case 3: FN<S_, 3>(__VA_ARGS__); break;                         \
+        case 4: FN<S_, 4>(__VA_ARGS__); break;                         \
+        default: FN<S_, 5>(__VA_ARGS__); break;                        \
+    }
+
+cudaError_t launch_sort_and_spread(tsne_plan* pl, const float* Y) {
+    if (pl->s == 2) { FITSNE_DISPATCH(2, sort_and_spread_impl, pl, Y); }
+    else { FITSNE_DISPATCH(1, sort_and_spread_impl, pl, Y); }
+    return cudaGetLastError();
+}
+
+template <int S, int PP, bool STEP>
+static void force_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha, float* dY,
+                       StepArgs sa) {
+    const int g = grid_for(pl, pl->N * 32, 256, 8);
+    force_kernel<S, PP, STEP><<<g, 256, 0, pl->stream>>>(P.row_ptr, P.col, P.val, Y, pl->params,
+                                                         pl->hgrid, alpha, dY, sa, pl->N);
+    pl->launches += 1;
+}
+
+template <int S, int PP>
+static void gradient_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,
+                          float* dY) {
+    force_impl<S, PP, false>(pl, P, Y, alpha, dY, StepArgs{});
+}
+
+template <int S, int PP>
+static void step_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,
+                      const StepArgs& sa) {
+    force_impl<S, PP, true>(pl, P, Y, alpha, nullptr, sa);
+}
+
+cudaError_t launch_gradient(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,
+                            float* dY) {
+    if (pl->s == 2) { FITSNE_DISPATCH(2, gradient_impl, pl, P, Y, alpha, dY); }
+    else { FITSNE_DISPATCH(1, gradient_impl, pl, P, Y, alpha, dY); }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(tsne_plan* pl, const tsne_csr& P, const float* Y, float* Y_new,
+                        float* uY, float* gains, float alpha, float momentum, float lr,
+                        float min_gain, float gain_inc, float gain_dec) {
+    StepArgs sa{Y_new, uY, gains, momentum, lr, min_gain, gain_inc, gain_dec};
+    if (pl->s == 2) { FITSNE_DISPATCH(2, step_impl, pl, P, Y, alpha, sa); }
+    else { FITSNE_DISPATCH(1, step_impl, pl, P, Y, alpha, sa); }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kl(tsne_plan* pl, const tsne_csr& P, const float* Y) {
+    const int g = 4 * pl->sm_count;  // kl_partial holds 2 doubles per block
+    if (pl->s == 2)
+        kl_kernel<2><<<g, 256, 0, pl->stream>>>(P.row_ptr, P.col, P.val, Y, pl->N, pl->params,
+                                                pl->kl_partial, pl->tickets + 3, pl->kl_out_dev);
+    else
+        kl_kernel<1><<<g, 256, 0, pl->stream>>>(P.row_ptr, P.col, P.val, Y, pl->N, pl->params,
+                                                pl->kl_partial, pl->tickets + 3, pl->kl_out_dev);
+    pl->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(tsne_plan* pl, const tsne_csr& P) {
+    const int g = grid_for(pl, pl->N, 256, 8);
+    validate_kernel<<<g, 256, 0, pl->stream>>>(P.row_ptr, P.col, P.val, pl->N, P.nnz,
+                                               pl->valid_flag);
+    pl->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(tsne_plan* pl, float* a, float v, int64_t n) {
+    const int g = grid_for(pl, n, 256, 8);
+    fill_kernel<<<g, 256, 0, pl->stream>>>(a, v, n);
+    pl->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace fitsne

@@ -1,0 +1,74 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+entry point include/fitsne_gb300.h declares; host-only entry points behave as
+documented (no device work is issued here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fitsne_gb300.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tsne_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1712_09005_gb300 import build
+    build.build()
+    from paper_1712_09005_gb300 import _abi
+    return _abi.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    from paper_1712_09005_gb300 import _abi
+    assert sorted(_abi.exported_names()) == declared_functions()
+
+
+def test_host_only_entry_points(lib):
+    from paper_1712_09005_gb300 import _abi
+    assert lib.tsne_version().startswith(b"fitsne-gb300")
+    sp = _abi.tsne_step_params()
+    lib.tsne_step_params_default(ctypes.byref(sp))
+    assert (sp.n_iter, sp.early_iters, sp.early_alpha, sp.lr) == (1000, 250, 12.0, 200.0)
+    sp.late_iters, sp.late_alpha = 250, 4.0
+    alphas = [lib.tsne_alpha_at(ctypes.byref(sp), i) for i in (0, 249, 250, 749, 750, 999)]
+    assert alphas == [12.0, 12.0, 1.0, 1.0, 4.0, 4.0]
+
+
+@pytest.mark.parametrize("N,s,n_int,p,n_int_max", [
+    (1, 2, 0, 3, 0),       # N < 2
+    (100, 3, 0, 3, 0),     # s not in {1, 2}
+    (100, 2, 0, 1, 0),     # p < 2
+    (100, 2, 0, 6, 0),     # p > 5
+    (100, 2, 0, 3, 401),   # p * n_int_max > 1200 in 2-D
+    (100, 1, 0, 3, 1001),  # p * n_int_max > 3000 in 1-D
+    (100, 2, 500, 3, 0),   # fixed count above the cap
+])
+def test_plan_create_rejects_bad_arguments(lib, N, s, n_int, p, n_int_max):
+    from paper_1712_09005_gb300 import _abi
+    opts = _abi.tsne_plan_opts(0, n_int_max, None)
+    out = ctypes.c_void_p(1)
+    rc = lib.tsne_plan_create(N, s, n_int, p, ctypes.byref(opts), ctypes.byref(out))
+    assert rc == _abi.TSNE_ERR_INVALID_ARG
+    assert out.value is None
+    assert lib.tsne_last_error_string()
+
+
+def test_null_plan_is_rejected(lib):
+    from paper_1712_09005_gb300 import _abi
+    assert lib.tsne_plan_destroy(None) == 0
+    assert lib.tsne_plan_status(None) == _abi.TSNE_ERR_INVALID_ARG
+    assert lib.tsne_plan_launch_count(None) == 0

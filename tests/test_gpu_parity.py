@@ -1,0 +1,290 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: dY relative L2 <= 1e-5, Z relative <= 1e-6 (FP32 spreading, FFT
+and gather against the FP64 oracle on the same box); the spread grids and the
+node potentials element by element relative to their largest magnitude.
+Sizes span many tiles with ragged tails (N not a multiple of 32 or 256).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1712_09005_gb300 as pkg
+from paper_1712_09005_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DY_TOL = 1e-5
+Z_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def clustered_Y(N, s, scale, seed, n_clusters=6):
+    """Embedding-like coordinates: clusters of relative width 0.1 around N(0, scale^2)."""
+    rng = np.random.default_rng(seed)
+    c = rng.normal(0, scale, size=(n_clusters, s))
+    lab = rng.integers(0, n_clusters, size=N)
+    return (c[lab] + rng.normal(0, 0.1 * scale, size=(N, s))).astype(np.float32)
+
+
+_P_CACHE = {}
+
+
+def affinities(N, seed, perp=30.0):
+    key = (N, seed, perp)
+    if key not in _P_CACHE:
+        X = inputs.mixture(N=N, n_clusters=6, seed=seed)
+        _P_CACHE[key] = inputs.affinities(X, perp, device="cpu")
+    return _P_CACHE[key]
+
+
+def oracle_opts(plan_s, n_int_fixed=0):
+    return oracle.InterpOptions(p=3, n_int_fixed=n_int_fixed, n_min=50,
+                                n_int_max=400 if plan_s == 2 else 1000, use_fft=True)
+
+
+CASES = [(2000, 20.0), (3001, 0.05), (1537, 90.0), (4099, 3.0)]
+
+
+@pytest.mark.parametrize("s", [1, 2])
+@pytest.mark.parametrize("N,scale", CASES)
+def test_gradient_and_Z(s, N, scale):
+    P = affinities(N, 1)
+    Y = clustered_Y(N, s, scale, seed=N + s)
+    with pkg.Plan(N, s) as plan:
+        Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+        Yd = torch.as_tensor(Y, device="cuda")
+        dY, Z = plan.gradient(Pd, Yd, alpha=12.0)
+        rep, _ = plan.gradient(Pd, Yd, alpha=0.0)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        info = plan.info()
+    ref = oracle.interp_gradient(Y.astype(np.float64), P.as_tuple(), alpha=12.0, opts=oracle_opts(s))
+    bx = ref["box"]
+    assert info["n_int"] == bx.n_int
+    assert np.float32(info["y_min"]) == np.float32(bx.y_min)
+    assert np.float32(info["b"]) == np.float32(bx.b)
+    assert info["fft_len"] >= 2 * bx.n_int * 3
+    assert rel_l2(dY.cpu().numpy(), ref["dY"]) <= DY_TOL
+    assert abs(Z.item() - ref["Z"]) <= Z_TOL * ref["Z"]
+    assert rel_l2(rep.cpu().numpy(), 4.0 * ref["rep"]) <= DY_TOL
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_spread_grids(s):
+    N = 2500
+    P = affinities(N, 2)
+    Y = clustered_Y(N, s, 15.0, seed=7)
+    with pkg.Plan(N, s) as plan:
+        Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+        plan.gradient(Pd, torch.as_tensor(Y, device="cuda"), alpha=1.0)
+        info = plan.info()
+        w = plan.debug(0)
+    ref = oracle.interp_gradient(Y.astype(np.float64), P.as_tuple(), opts=oracle_opts(s),
+                                 want_grids=True)
+    n = info["n"]
+    G = n ** s
+    w = w.reshape(s + 1, G).astype(np.float64)
+    rw = ref["w"].reshape(s + 1, G)
+    c = np.float64(np.float32(np.float32(info["y_min"]) + np.float32(0.5) * np.float32(info["width"])))
+    expect = [rw[0]] + [rw[m] - c * rw[0] for m in range(1, s + 1)]
+    for ch in range(s + 1):
+        scale = np.abs(expect[ch]).max()
+        assert np.abs(w[ch] - expect[ch]).max() <= 2e-6 * scale, ch
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_fft_convolution_against_cufft(s):
+    """The hand-written FFT convolution equals cuFFT (torch.fft, FP64) on the same grids."""
+    N = 3000
+    P = affinities(N, 3)
+    Y = clustered_Y(N, s, 40.0, seed=11)
+    with pkg.Plan(N, s) as plan:
+        Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+        plan.gradient(Pd, torch.as_tensor(Y, device="cuda"), alpha=1.0)
+        info = plan.info()
+        w = plan.debug(0)
+        h = plan.debug(1)
+    n, delta = info["n"], np.float64(info["delta"])
+    L = 2 * n
+    dev = torch.device("cuda")
+    off = torch.arange(L, device=dev, dtype=torch.float64)
+    off = torch.where(off < n, off, off - L)  # offsets; index n is never reached
+    if s == 1:
+        r2 = (off * delta) ** 2
+        wg = torch.as_tensor(w.reshape(2, n), device=dev, dtype=torch.float64)
+        pad = torch.zeros((2, L), dtype=torch.float64, device=dev)
+        pad[:, :n] = wg
+        K1 = 1 / (1 + r2)
+        F = torch.fft.fft(pad)
+        conv = lambda a, K: torch.fft.ifft(F[a] * torch.fft.fft(K)).real[:n]
+        want = torch.stack([conv(0, K1), conv(1, K1 ** 2), torch.zeros(n, dtype=torch.float64, device=dev),
+                            conv(0, K1 ** 2)], dim=1)
+    else:
+        r2 = (off[:, None] * delta) ** 2 + (off[None, :] * delta) ** 2
+        wg = torch.as_tensor(w.reshape(3, n, n), device=dev, dtype=torch.float64)
+        pad = torch.zeros((3, L, L), dtype=torch.float64, device=dev)
+        pad[:, :n, :n] = wg
+        K1 = 1 / (1 + r2)
+        F = torch.fft.fft2(pad)
+        conv = lambda a, K: torch.fft.ifft2(F[a] * torch.fft.fft2(K)).real[:n, :n].reshape(-1)
+        want = torch.stack([conv(0, K1), conv(1, K1 ** 2), conv(2, K1 ** 2), conv(0, K1 ** 2)], dim=1)
+    want = want.cpu().numpy()
+    for k in ([0, 1, 3] if s == 1 else [0, 1, 2, 3]):
+        scale = np.abs(want[:, k]).max()
+        assert np.abs(h[:, k] - want[:, k]).max() <= 5e-6 * scale, k
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_points_on_nodes_match_exact(s):
+    """Forced box [0, 6], 8 intervals, delta = 1/4: nodes are exact floats, so
+    the interpolated gradient equals the exact O(N^2) one up to FP32 rounding."""
+    rng = np.random.default_rng(5)
+    N = 700
+    g = rng.integers(0, 24, size=(N, s))
+    Y = ((g + 0.5) * 0.25).astype(np.float32)
+    P = affinities(N, 4, perp=10.0)
+    with pkg.Plan(N, s) as plan:
+        plan.set_box(0.0, 6.0, 8)
+        Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+        dY, Z = plan.gradient(Pd, torch.as_tensor(Y, device="cuda"), alpha=2.0)
+        torch.cuda.synchronize()
+    ex = oracle.exact_gradient(Y.astype(np.float64), P.as_tuple(), alpha=2.0)
+    assert rel_l2(dY.cpu().numpy(), ex["dY"]) <= DY_TOL
+    assert abs(Z.item() - ex["Z"]) <= Z_TOL * ex["Z"]
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_step_matches_oracle_step(s):
+    N = 2100
+    P = affinities(N, 5)
+    rng = np.random.default_rng(9)
+    Y = clustered_Y(N, s, 10.0, seed=13)
+    uY = (rng.normal(0, 0.05, size=(N, s))).astype(np.float32)
+    gains = rng.uniform(0.5, 2.0, size=(N, s)).astype(np.float32)
+    sched = pkg.Schedule()
+    with pkg.Plan(N, s) as plan:
+        Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+        Yd, ud, gd = (torch.as_tensor(a.copy(), device="cuda") for a in (Y, uY, gains))
+        plan.step(Pd, Yd, ud, gd, 300, sched)
+        torch.cuda.synchronize()
+    ref = oracle.interp_gradient(Y.astype(np.float64), P.as_tuple(), alpha=1.0, opts=oracle_opts(s))
+    Yo, uo, go = Y.astype(np.float64), uY.astype(np.float64), gains.astype(np.float64)
+    oracle.step(Yo, uo, go, ref["dY"], oracle.Schedule(), 300)
+    # an update moves Y by lr * gain * dY; the dY tolerance bounds the difference
+    step_scale = np.linalg.norm(200.0 * go * ref["dY"])
+    assert np.linalg.norm(Yd.cpu().numpy() - Yo) <= 2 * DY_TOL * step_scale + 1e-6 * np.linalg.norm(Yo)
+    # gains follow the sign rule exactly wherever the signs agree
+    same = np.sign(ref["dY"]) != 0
+    assert (np.abs(gd.cpu().numpy() - go)[same] < 1e-6).mean() > 0.999
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_kl(s):
+    N = 2400
+    P = affinities(N, 6)
+    Y = clustered_Y(N, s, 12.0, seed=17)
+    with pkg.Plan(N, s) as plan:
+        Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+        kl = plan.kl(Pd, torch.as_tensor(Y, device="cuda"))
+    ref = oracle.interp_gradient(Y.astype(np.float64), P.as_tuple(), opts=oracle_opts(s))
+    want = oracle.kl(Y.astype(np.float64), P.as_tuple(), ref["Z"])
+    assert abs(kl - want) <= 1e-6 * abs(want)
+
+
+def test_two_points_and_degenerate_box():
+    # N = 2 (the smallest plan), and all points on one location (width 0 -> 1)
+    P = (np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.array([0.5, 0.5], np.float32))
+    for Y in (np.array([[0.3, -0.2], [1.3, 0.8]], np.float32), np.full((2, 2), 4.0, np.float32)):
+        with pkg.Plan(2, 2) as plan:
+            dY, Z = plan.gradient(pkg.DeviceCSR.from_host(*P), torch.as_tensor(Y, device="cuda"), 3.0)
+            torch.cuda.synchronize()
+        ref = oracle.interp_gradient(Y.astype(np.float64), P, alpha=3.0, opts=oracle_opts(2))
+        np.testing.assert_allclose(dY.cpu().numpy(), ref["dY"], rtol=1e-5, atol=1e-6)
+        assert abs(Z.item() - ref["Z"]) <= 1e-5 * abs(ref["Z"])
+
+
+def test_empty_rows_and_ragged():
+    rng = np.random.default_rng(21)
+    N = 1031
+    Y = clustered_Y(N, 2, 25.0, seed=3)
+    # rows with no neighbours, and a few heavy rows
+    rows, cols = [], []
+    for i in range(N):
+        k = 0 if i % 7 == 0 else (200 if i % 101 == 0 else 5)
+        nb = rng.choice(np.delete(np.arange(N), i), size=k, replace=False)
+        rows += [i] * k
+        cols += list(nb)
+    import scipy.sparse as sp
+    A = sp.csr_matrix((rng.random(len(rows)), (rows, cols)), shape=(N, N))
+    A = A + A.T
+    A = (A / A.sum()).tocsr()
+    A.sort_indices()
+    P = (A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float32))
+    with pkg.Plan(N, 2) as plan:
+        dY, Z = plan.gradient(pkg.DeviceCSR.from_host(*P), torch.as_tensor(Y, device="cuda"), 5.0)
+        torch.cuda.synchronize()
+    ref = oracle.interp_gradient(Y.astype(np.float64), P, alpha=5.0, opts=oracle_opts(2))
+    assert rel_l2(dY.cpu().numpy(), ref["dY"]) <= DY_TOL
+
+
+def test_interval_cap_and_fixed_count():
+    N = 1200
+    P = affinities(N, 7)
+    Y = clustered_Y(N, 2, 400.0, seed=23)  # width far above the 2-D cap of 400
+    for fixed in (0, 37):
+        with pkg.Plan(N, 2, n_intervals=fixed) as plan:
+            dY, Z = plan.gradient(pkg.DeviceCSR.from_host(*P.as_tuple()), torch.as_tensor(Y, device="cuda"), 1.0)
+            info = plan.info()
+        ref = oracle.interp_gradient(Y.astype(np.float64), P.as_tuple(), opts=oracle_opts(2, fixed))
+        assert info["n_int"] == ref["box"].n_int == (400 if fixed == 0 else 37)
+        assert rel_l2(dY.cpu().numpy(), ref["dY"]) <= DY_TOL
+
+
+def test_errors_are_reported():
+    with pytest.raises(pkg.TsneError) as e:
+        pkg.Plan(100, 3)
+    assert e.value.code == pkg._abi.TSNE_ERR_INVALID_ARG
+    with pytest.raises(pkg.TsneError):
+        pkg.Plan(100, 2, p=1)
+    with pytest.raises(pkg.TsneError):
+        pkg.Plan(1, 2)
+    N = 300
+    P = affinities(N, 8, perp=10.0)
+    Y = clustered_Y(N, 2, 5.0, seed=1)
+    Y[17, 1] = np.nan
+    with pkg.Plan(N, 2) as plan:
+        Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+        plan.gradient(Pd, torch.as_tensor(Y, device="cuda"), 1.0)
+        assert plan.status() == pkg._abi.TSNE_ERR_NONFINITE
+        assert plan.status() == 0  # the latch clears
+        bad_col = P.col.copy()
+        bad_col[5] = N + 3
+        with pytest.raises(pkg.TsneError):
+            plan.validate(pkg.DeviceCSR.from_host(P.row_ptr, bad_col, P.val))
+        plan.validate(Pd)
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_run_host_equals_run(s):
+    N = 1500
+    P = affinities(N, 9)
+    Y0 = inputs.initial_embedding(N, s, seed=4)
+    sched = pkg.Schedule(n_iter=20)
+    with pkg.Plan(N, s) as plan:
+        Yd = torch.as_tensor(Y0.copy(), device="cuda")
+        kl_d = plan.run(pkg.DeviceCSR.from_host(*P.as_tuple()), Yd, sched)
+        Yh = Y0.copy()
+        kl_h = plan.run_host(P.row_ptr, P.col, P.val, Yh, sched)
+    assert abs(kl_d - kl_h) <= 1e-5 * abs(kl_d)
+    np.testing.assert_allclose(Yh, Yd.cpu().numpy(), rtol=1e-4, atol=1e-6)
