@@ -217,11 +217,16 @@ int tsne_plan_info(tsne_plan* plan, tsne_plan_info_t* out);
 
 /*
  * Copies an internal buffer of the most recent evaluation to HOST memory,
- * for tests (synchronises). which:
- *   0  spread grids w, fp32 [(s+1) x n^s], charges (1, y(1) - c, .., y(s) - c)
- *      with c = y_min + width / 2 (the centring is exact: spreading is linear)
- *   1  potentials at the nodes, fp32 [n^s x 4] = (h_1, h_2, h_3, h_{s+2}) with
- *      h_3 = 0 when s = 1, the charges as in 0
+ * for tests (synchronises). Nodes are indexed g = (g_1, g_2), row-major; a
+ * node's position is y_min + (g + 1/2) delta; t is a point's coordinate
+ * inside its box in units of delta and j the node's index in the box.
+ *   0  spread grids as FP64 [(s+1) x n^s] (accumulated exactly on the device
+ *      in fixed point): w0 = sum_i L_g(y_i) and the dipole grids
+ *      d_m = sum_i L_g(y_i) (t_m - j_m - 1/2) = (w_{y(m)} - y~_g(m) w0) / delta
+ *   1  node values, fp32 [n^s x 4] = (h_1, u'_1, u'_2, v) with h_1 = K1 * w0,
+ *      v = K2 * w0 (= h_{s+2} at the nodes), u'_m = K2 * d_m - G_m * w0 with
+ *      G_m(o) = o_m K2(o delta), i.e. (v_{m+1} - y~(m) v) / delta; u'_2 = 0
+ *      when s = 1
  *   2  bucket offsets, int32 [n_int^s + 1] (points per box, exclusive scan)
  * bytes must be at least the size above; the size needed is returned in
  * *bytes_needed (may be NULL).

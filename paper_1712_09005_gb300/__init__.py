@@ -177,7 +177,7 @@ def tsne_debug_copy(plan, which: int, s: int) -> np.ndarray:
     elif which == 1:
         out = np.empty((need.value // 16, 4), dtype=np.float32)
     else:
-        out = np.empty(need.value // 4, dtype=np.float32)
+        out = np.empty(need.value // 8, dtype=np.float64)
     check(lib().tsne_debug_copy(plan, which, ctypes.c_void_p(out.ctypes.data), out.nbytes, None))
     return out
 

@@ -167,6 +167,29 @@ int check_vec(const tsne_plan* pl, const void* p, const char* name) {
     return TSNE_OK;
 }
 
+// Binary point of the fixed-point spread: every spread value is a sum over
+// at most N points of W (t - j - 1/2) or W, |W| <= lmax^s with lmax the
+// largest Lagrange basis value on [0, p], |t - j - 1/2| <= p - 1/2. The shift
+// keeps N times twice that bound below 2^62.
+int fixed_point_shift(int64_t N, int s, int p) {
+    double lmax = 0.0;
+    for (int k = 0; k <= 4000; ++k) {
+        const double t = p * (double)k / 4000.0;
+        for (int j = 0; j < p; ++j) {
+            double num = 1.0, den = 1.0;
+            for (int m = 0; m < p; ++m) {
+                if (m == j) continue;
+                num *= t - (m + 0.5);
+                den *= (double)(j - m);
+            }
+            lmax = std::max(lmax, fabs(num / den));
+        }
+    }
+    const double C = pow(lmax, s) * std::max(1.0, p - 0.5) * 2.0;
+    int shift = (int)floor(62.0 - log2((double)N * C));
+    return std::min(shift, 60);
+}
+
 float alpha_at(const tsne_step_params* sp, int it) {
     if (it < sp->early_iters) return sp->early_alpha;
     if (sp->late_iters > 0 && it >= sp->n_iter - sp->late_iters) return sp->late_alpha;
@@ -244,6 +267,7 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     pl->n_int_max = n_int_max;
     pl->stream = (cudaStream_t)o.stream;
     pl->n_max = p * n_int_max;
+    pl->fx_shift = fixed_point_shift(N, s, p);
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -281,7 +305,7 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     ALLOC(block_chunks, pl->scan_blocks);
     ALLOC(sorted_y, N * s);
     ALLOC(w, (s + 1) * G);
-    if (s == 2) ALLOC(spec, 3 * (int64_t)pl->n_max * pl->L_max);
+    if (s == 2) ALLOC(spec, 4 * (int64_t)pl->n_max * pl->L_max);
     ALLOC(hgrid, G);
     ALLOC(z_partial, pl->n_max);
     ALLOC(kl_partial, 2 * kl_blocks);
@@ -537,17 +561,28 @@ int tsne_debug_copy(tsne_plan* plan, int32_t which, void* host_dst, size_t bytes
        "params read-back");
     CU(cudaStreamSynchronize(plan->stream), "debug synchronise");
     const int64_t G = (plan->s == 2) ? (int64_t)P.n * P.n : P.n;
-    const void* src = nullptr;
     size_t need = 0;
     switch (which) {
-        case 0: src = plan->w; need = sizeof(float) * (plan->s + 1) * G; break;
-        case 1: src = plan->hgrid; need = sizeof(float4) * G; break;
-        case 2: src = plan->box_start; need = sizeof(int32_t) * (P.n_boxes + 1); break;
+        case 0: need = sizeof(double) * (plan->s + 1) * G; break;
+        case 1: need = sizeof(float4) * G; break;
+        case 2: need = sizeof(int32_t) * (P.n_boxes + 1); break;
         default: return fail(TSNE_ERR_INVALID_ARG, "unknown buffer %d", which);
     }
     if (bytes_needed) *bytes_needed = need;
     if (!host_dst) return TSNE_OK;
     if (bytes < need) return fail(TSNE_ERR_INVALID_ARG, "buffer too small (%zu < %zu)", bytes, need);
+    if (which == 0) {
+        std::vector<long long> raw((size_t)((plan->s + 1) * G));
+        CU(cudaMemcpyAsync(raw.data(), plan->w, sizeof(long long) * raw.size(),
+                           cudaMemcpyDeviceToHost, plan->stream),
+           "debug copy");
+        CU(cudaStreamSynchronize(plan->stream), "debug synchronise");
+        double* out = static_cast<double*>(host_dst);
+        const double inv = ldexp(1.0, -P.fx_shift);
+        for (size_t k = 0; k < raw.size(); ++k) out[k] = (double)raw[k] * inv;
+        return TSNE_OK;
+    }
+    const void* src = which == 1 ? (const void*)plan->hgrid : (const void*)plan->box_start;
     CU(cudaMemcpyAsync(host_dst, src, need, cudaMemcpyDeviceToHost, plan->stream), "debug copy");
     CU(cudaStreamSynchronize(plan->stream), "debug synchronise");
     return TSNE_OK;

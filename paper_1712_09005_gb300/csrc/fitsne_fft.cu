@@ -4,25 +4,31 @@
 // hand-written shared-memory FFT (mixed-radix 2/3/4/5 Stockham, FP32,
 // twiddles rounded from FP64).
 //
-// The s+1 charge grids w (charges 1, y(1)-c, .., y(s)-c) are convolved with
-// K1 = (1+r^2)^-1 and K2 = K1^2 sampled at the node offsets, giving the s+2
-// node potentials of the Appendix:
-//   h1 = K1 * w_1,  h_{m+1} = K2 * w_{y(m)},  h_{s+2} = K2 * w_1.
+// Inputs (node units, offsets o in units of delta): the charge grid w0 and
+// the dipole grids d_m = sum L_g(y)(t_m - j_m - 1/2) from the spread. The
+// Appendix needs h1 = K1 * w0, v_{m+1} = K2 * w_{y(m)} and v_{s+2} = K2 * w0;
+// with w_{y(m)} = delta d_m + y~(m) w0 the combination the gradient uses,
+//   u_m[g] = v_{m+1}[g] - y~_g(m) v_{s+2}[g] = delta (K2 * d_m - G_m * w0)[g],
+// G_m(o) = o_m K2(o), follows by expanding y~_g'(m) = y~_g(m) - delta (g - g')_m
+// (exact). The transforms therefore produce, per node,
+//   (h1, u'_1, u'_2, v_{s+2}) = (K1 * w0, K2 * d_1 - G_1 * w0, K2 * d_2 - G_2 * w0, K2 * w0)
+// with u_m = delta u'_m; no output is a small difference of large values.
+//
 // Real signals are packed in pairs into complex transforms:
-//   C0 = w_1 + i w_{y1}, C1 = w_{y2} (+ i 0), CK = K1 + i K2.
-// K1 and K2 are even in every offset, so their spectra are real and even and
-// come out of one transform as Re / Im. The inverse transforms pack the
-// real results the same way: D0 = V1 + i V2 -> (h1, h2), D1 = V3 + i V4 ->
-// (h3, h_{s+2}).
+//   C0 = w0 + i d_1, C1 = d_2 (+ i 0), CK = K1 + i K2, CG = G_1 + i G_2.
+// K1, K2 are even in every offset (real, even spectra: Re / Im of one
+// transform); G_m is odd in offset m and even in the other (imaginary
+// spectrum i S_m), so the spectrum of CG is i S_1 - S_2. Outputs are packed
+// the same way: D0 = H1 + i U1 -> (h1, u'_1), D1 = U2 + i V -> (u'_2, v).
 //
 // 2-D passes (one CTA per work item, grid-stride):
-//   rows_fwd_kernel  FFT along dimension 2 of the n rows of C0, C1 and of the
-//                    n distinct kernel rows (|offset| < n)
+//   rows_fwd_kernel  FFT along dimension 2 of the n rows of C0, C1, and of
+//                    the rows o1 = 0..n-1 of CK and CG (the rows o1 < 0
+//                    follow by symmetry)
 //   cols_kernel      per column pair (k2, L-k2): FFT along dimension 1,
-//                    split the packed spectra, multiply by the kernel
-//                    spectra, pack, inverse FFT along dimension 1
-//   rows_inv_kernel  inverse FFT of the n needed rows, write the node
-//                    potentials, and the FP64 partial sums of Z = w_1 . h1 - N
+//                    split the packed spectra, multiply, pack, inverse FFT
+//   rows_inv_kernel  inverse FFT of the n needed rows, node values, and the
+//                    FP64 partial sums of Z = w0 . h1 - N
 // 1-D: conv1d_kernel does the whole convolution in one CTA.
 #include <math.h>
 
@@ -163,6 +169,9 @@ __device__ __forceinline__ float2 kernel_pair(float delta2, int d2) {
     return make_float2(k1, k1 * k1);
 }
 
+// Fixed-point spread value to FP32.
+__device__ __forceinline__ float fx(long long v, float inv) { return __ll2float_rn(v) * inv; }
+
 // Signed node offset represented by circulant index i (|offset| < n), or -1
 // for the gap that outputs in [0, n) never reach.
 __device__ __forceinline__ int circ_offset(int i, int n, int L) {
@@ -172,11 +181,12 @@ __device__ __forceinline__ int circ_offset(int i, int n, int L) {
 }  // namespace
 
 // ----------------------------------------------------------------------------
-// 2-D, pass 1: row FFTs. Work item m < 3n: type m / n (0: C0, 1: C1, 2: CK),
-// row m % n. Output rows of length L, row-major, at spec + type n L.
+// 2-D, pass 1: row FFTs. Work item m < 4n: type m / n (0: C0, 1: C1, 2: CK,
+// 3: CG), row r = m % n (for CK and CG the offset o1 = r >= 0). Output rows of
+// length L, row-major, at spec + type n L.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-rows_fwd_kernel(const float* __restrict__ w, const Params* __restrict__ params,
+rows_fwd_kernel(const long long* __restrict__ w, const Params* __restrict__ params,
                 const FftEntry* __restrict__ table, const float2* __restrict__ tw_all,
                 float2* __restrict__ spec) {
     extern __shared__ float2 sm[];
@@ -188,19 +198,28 @@ rows_fwd_kernel(const float* __restrict__ w, const Params* __restrict__ params,
     const int n = P.n, L = P.L;
     const int64_t G = (int64_t)n * n;
     const float2* tw = tw_all + e.tw_off;
+    const float inv = P.fx_inv;
     float2* A = sm;
     float2* B = sm + L;
-    for (int m = blockIdx.x; m < 3 * n; m += gridDim.x) {
+    for (int m = blockIdx.x; m < 4 * n; m += gridDim.x) {
         const int type = m / n, r = m - type * n;
         for (int c = threadIdx.x; c < L; c += blockDim.x) {
             float2 v = make_float2(0.0f, 0.0f);
             if (type == 0) {
-                if (c < n) v = make_float2(w[(int64_t)r * n + c], w[G + (int64_t)r * n + c]);
+                if (c < n) v = make_float2(fx(w[(int64_t)r * n + c], inv), fx(w[G + (int64_t)r * n + c], inv));
             } else if (type == 1) {
-                if (c < n) v = make_float2(w[2 * G + (int64_t)r * n + c], 0.0f);
+                if (c < n) v = make_float2(fx(w[2 * G + (int64_t)r * n + c], inv), 0.0f);
             } else {
                 const int o = circ_offset(c, n, L);
-                if (o >= 0) v = kernel_pair(P.delta2, r * r + o * o);
+                if (o >= 0) {
+                    const float2 k = kernel_pair(P.delta2, r * r + o * o);
+                    if (type == 2) {
+                        v = k;
+                    } else {
+                        const int o2 = (c < n) ? c : c - L;  // signed offset
+                        v = make_float2((float)r * k.y, (float)o2 * k.y);
+                    }
+                }
             }
             A[c] = v;
         }
@@ -213,9 +232,14 @@ rows_fwd_kernel(const float* __restrict__ w, const Params* __restrict__ params,
 }
 
 // ----------------------------------------------------------------------------
-// 2-D, pass 2: column pairs (k2, L - k2), k2 = 0 .. L/2. Forward FFT of the
-// five columns, spectra products, inverse FFT of the four packed results,
-// which overwrite the first n rows of columns k2 and L - k2 of C0 and C1.
+// 2-D, pass 2: column pairs (k2, L - k2), k2 = 0 .. L/2. Forward FFT of six
+// columns (C0 and C1 at k2 and L - k2, CK and CG at k2), spectra products,
+// inverse FFT of the four packed results, which overwrite the first n rows of
+// columns k2 and L - k2 of C0 and C1.
+// Rows o1 < 0 of the kernels: CK row -r = CK row r (even); the CG row
+// spectrum is real with X_{-r}[k2] = -X_r[L - k2] (G_1 odd, G_2 even in o1).
+// At column L - k2 the kernel spectra are K^(k1, k2), S_1(k1, k2) and
+// -S_2(k1, k2) (G_2 is odd in o2).
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(512)
 cols_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ table,
@@ -231,41 +255,59 @@ cols_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ tabl
     float2* C0 = spec;
     float2* C1 = spec + (int64_t)n * L;
     const float2* CK = spec + 2 * (int64_t)n * L;
+    const float2* CG = spec + 3 * (int64_t)n * L;
     float2* X = sm;
-    float2* Yb = sm + 5 * L;
+    float2* Yb = sm + 6 * L;
+    const float2 z = make_float2(0.0f, 0.0f);
     for (int k2 = blockIdx.x; k2 <= L / 2; k2 += gridDim.x) {
         const int k2b = (L - k2) % L;
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
             const bool in = i < n;
-            const float2 z = make_float2(0.0f, 0.0f);
             X[i] = in ? C0[(int64_t)i * L + k2] : z;
             X[L + i] = in ? C0[(int64_t)i * L + k2b] : z;
             X[2 * L + i] = in ? C1[(int64_t)i * L + k2] : z;
             X[3 * L + i] = in ? C1[(int64_t)i * L + k2b] : z;
-            const int o = circ_offset(i, n, L);
-            X[4 * L + i] = o >= 0 ? CK[(int64_t)o * L + k2] : z;
+            float2 ck = z, cg = z;
+            if (in) {
+                ck = CK[(int64_t)i * L + k2];
+                cg = CG[(int64_t)i * L + k2];
+            } else if (i > L - n) {
+                ck = CK[(int64_t)(L - i) * L + k2];
+                const float2 t = CG[(int64_t)(L - i) * L + k2b];
+                cg = make_float2(-t.x, -t.y);
+            }
+            X[4 * L + i] = ck;
+            X[5 * L + i] = cg;
         }
         __syncthreads();
-        float2* F = fft_batch(X, Yb, e, 5, tw, -1.0f);
+        float2* F = fft_batch(X, Yb, e, 6, tw, -1.0f);
         float2* O = (F == X) ? Yb : X;
         for (int k1 = threadIdx.x; k1 < L; k1 += blockDim.x) {
             const int k1n = (L - k1) % L;
             const float2 xa = F[k1], xb = F[L + k1];
             const float2 xa_m = F[k1n], xb_m = F[L + k1n];
-            // unpack C0 = w_1 + i w_{y1} at (k1, k2) and (k1, L - k2)
-            const float2 w1a = cscale(cadd(xa, conjf2(xb_m)), 0.5f);
-            const float2 dya = csub(xa, conjf2(xb_m));
-            const float2 wya = make_float2(0.5f * dya.y, -0.5f * dya.x);
-            const float2 w1b = cscale(cadd(xb, conjf2(xa_m)), 0.5f);
-            const float2 dyb = csub(xb, conjf2(xa_m));
-            const float2 wyb = make_float2(0.5f * dyb.y, -0.5f * dyb.x);
-            const float2 w2a = F[2 * L + k1], w2b = F[3 * L + k1];
-            const float2 ck = F[4 * L + k1];  // (K1^, K2^), equal at L - k2
-            const float K1 = ck.x, K2 = ck.y;
-            O[k1] = cadd(cscale(w1a, K1), mul_si(cscale(wya, K2), 1.0f));
-            O[L + k1] = cadd(cscale(w1b, K1), mul_si(cscale(wyb, K2), 1.0f));
-            O[2 * L + k1] = cadd(cscale(w2a, K2), mul_si(cscale(w1a, K2), 1.0f));
-            O[3 * L + k1] = cadd(cscale(w2b, K2), mul_si(cscale(w1b, K2), 1.0f));
+            // C0 = w0 + i d_1 split at (k1, k2) [a] and (k1, L - k2) [b]
+            const float2 w0a = cscale(cadd(xa, conjf2(xb_m)), 0.5f);
+            const float2 ta = csub(xa, conjf2(xb_m));
+            const float2 d1a = make_float2(0.5f * ta.y, -0.5f * ta.x);
+            const float2 w0b = cscale(cadd(xb, conjf2(xa_m)), 0.5f);
+            const float2 tb = csub(xb, conjf2(xa_m));
+            const float2 d1b = make_float2(0.5f * tb.y, -0.5f * tb.x);
+            const float2 d2a = F[2 * L + k1], d2b = F[3 * L + k1];
+            const float2 ck = F[4 * L + k1];      // (K1^, K2^)
+            const float2 cg = F[5 * L + k1];      // i S1 - S2
+            const float K1 = ck.x, K2 = ck.y, S1 = cg.y, S2 = -cg.x;
+            // a: H1 = w0 K1, U1 = d1 K2 - i S1 w0, U2 = d2 K2 - i S2 w0, V = w0 K2
+            const float2 h1a = cscale(w0a, K1), va = cscale(w0a, K2);
+            const float2 u1a = csub(cscale(d1a, K2), mul_si(w0a, S1));
+            const float2 u2a = csub(cscale(d2a, K2), mul_si(w0a, S2));
+            const float2 h1b = cscale(w0b, K1), vb = cscale(w0b, K2);
+            const float2 u1b = csub(cscale(d1b, K2), mul_si(w0b, S1));
+            const float2 u2b = cadd(cscale(d2b, K2), mul_si(w0b, S2));
+            O[k1] = cadd(h1a, mul_si(u1a, 1.0f));
+            O[L + k1] = cadd(h1b, mul_si(u1b, 1.0f));
+            O[2 * L + k1] = cadd(u2a, mul_si(va, 1.0f));
+            O[3 * L + k1] = cadd(u2b, mul_si(vb, 1.0f));
         }
         __syncthreads();
         const float2* R = fft_batch(O, F, e, 4, tw, 1.0f);
@@ -309,10 +351,10 @@ __device__ void publish_Z(const double* __restrict__ z_partial, int rows, Params
 
 // ----------------------------------------------------------------------------
 // 2-D, pass 3: inverse row FFTs of the first n rows of D0 and D1; node
-// potentials (h1, h2, h3, h4) / L^2 for columns < n; FP64 row sums of w_1 h1.
+// values (h1, u'_1, u'_2, v) / L^2 for columns < n; FP64 row sums of w0 h1.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-rows_inv_kernel(const float* __restrict__ w, Params* params, const FftEntry* __restrict__ table,
+rows_inv_kernel(const long long* __restrict__ w, Params* params, const FftEntry* __restrict__ table,
                 const float2* __restrict__ tw_all, const float2* __restrict__ spec,
                 float4* __restrict__ hgrid, double* __restrict__ z_partial,
                 unsigned* __restrict__ ticket, double* Z_out, int64_t N) {
@@ -343,10 +385,10 @@ rows_inv_kernel(const float* __restrict__ w, Params* params, const FftEntry* __r
                 const float2 a = R[c], b = R[L + c];
                 const float4 h = make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
                 hgrid[(int64_t)r * n + c] = h;
-                zp += (double)w[(int64_t)r * n + c] * (double)h.x;
+                zp += (double)w[(int64_t)r * n + c] * (double)h.x;  // w0 in units of 2^-fx_shift
             }
             const double t = block_sum_d(zp, sred);
-            if (threadIdx.x == 0) z_partial[r] = t;
+            if (threadIdx.x == 0) z_partial[r] = t * (double)P.fx_inv;
             __syncthreads();
         }
     }
@@ -362,12 +404,14 @@ rows_inv_kernel(const float* __restrict__ w, Params* params, const FftEntry* __r
 }
 
 // ----------------------------------------------------------------------------
-// 1-D: the whole convolution in one CTA. C0 = w_1 + i w_y and CK = K1 + i K2
-// forward; D0 = W1 K1^ + i Wy K2^ and D1 = W1 K2^ inverse; node potentials
-// (h1, h2, 0, h3) / L; Z = w_1 . h1 - N in FP64.
+// 1-D: the whole convolution in one CTA. Forward: C0 = w0 + i d_1 and
+// CK' = (K1 + G_1) + i K2, whose spectrum is K1^ + i (S_1 + K2^); K2^ is the
+// even and S_1 the odd part of the imaginary part in k. Products as in 2-D;
+// inverse: D0 = H1 + i U1 -> (h1, u'_1), D1 = V -> v. Node values
+// (h1, u'_1, 0, v) / L; Z = w0 . h1 - N in FP64.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-conv1d_kernel(const float* __restrict__ w, Params* params, const FftEntry* __restrict__ table,
+conv1d_kernel(const long long* __restrict__ w, Params* params, const FftEntry* __restrict__ table,
               const float2* __restrict__ tw_all, float4* __restrict__ hgrid, double* Z_out,
               int64_t N) {
     extern __shared__ float2 sm[];
@@ -379,12 +423,19 @@ conv1d_kernel(const float* __restrict__ w, Params* params, const FftEntry* __res
     __syncthreads();
     const int n = P.n, L = P.L;
     const float2* tw = tw_all + e.tw_off;
+    const float inv = P.fx_inv;
     float2* X = sm;
     float2* Yb = sm + 2 * L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        X[i] = i < n ? make_float2(w[i], w[n + i]) : make_float2(0.0f, 0.0f);
+        X[i] = i < n ? make_float2(fx(w[i], inv), fx(w[n + i], inv)) : make_float2(0.0f, 0.0f);
         const int o = circ_offset(i, n, L);
-        X[L + i] = o >= 0 ? kernel_pair(P.delta2, o * o) : make_float2(0.0f, 0.0f);
+        float2 kv = make_float2(0.0f, 0.0f);
+        if (o >= 0) {
+            const float2 k = kernel_pair(P.delta2, o * o);
+            const int so = (i < n) ? i : i - L;  // signed offset
+            kv = make_float2(k.x + (float)so * k.y, k.y);
+        }
+        X[L + i] = kv;
     }
     __syncthreads();
     float2* F = fft_batch(X, Yb, e, 2, tw, -1.0f);
@@ -392,12 +443,14 @@ conv1d_kernel(const float* __restrict__ w, Params* params, const FftEntry* __res
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
         const int kn = (L - k) % L;
         const float2 x = F[k], xm = conjf2(F[kn]);
-        const float2 w1 = cscale(cadd(x, xm), 0.5f);
-        const float2 d = csub(x, xm);
-        const float2 wy = make_float2(0.5f * d.y, -0.5f * d.x);
-        const float2 ck = F[L + k];
-        O[k] = cadd(cscale(w1, ck.x), mul_si(cscale(wy, ck.y), 1.0f));
-        O[L + k] = cscale(w1, ck.y);
+        const float2 w0 = cscale(cadd(x, xm), 0.5f);
+        const float2 t = csub(x, xm);
+        const float2 d1 = make_float2(0.5f * t.y, -0.5f * t.x);
+        const float2 ck = F[L + k], ckn = F[L + kn];
+        const float K1 = ck.x, K2 = 0.5f * (ck.y + ckn.y), S1 = 0.5f * (ck.y - ckn.y);
+        const float2 u1 = csub(cscale(d1, K2), mul_si(w0, S1));
+        O[k] = cadd(cscale(w0, K1), mul_si(u1, 1.0f));
+        O[L + k] = cscale(w0, K2);
     }
     __syncthreads();
     const float2* R = fft_batch(O, F, e, 2, tw, 1.0f);
@@ -410,7 +463,7 @@ conv1d_kernel(const float* __restrict__ w, Params* params, const FftEntry* __res
     }
     const double t = block_sum_d(zp, sred);
     if (threadIdx.x == 0) {
-        const double Z = t - (double)N;
+        const double Z = t * (double)P.fx_inv - (double)N;
         params->Z = Z;
         params->inv_Z = (float)(1.0 / Z);
         if (Z_out) *Z_out = Z;
@@ -422,7 +475,7 @@ conv1d_kernel(const float* __restrict__ w, Params* params, const FftEntry* __res
 // sequence serves every iteration whatever N_int the box rule picks.
 // ----------------------------------------------------------------------------
 static size_t smem_rows_fwd(const tsne_plan* pl) { return sizeof(float2) * 2 * pl->L_max; }
-static size_t smem_cols(const tsne_plan* pl) { return sizeof(float2) * 10 * pl->L_max; }
+static size_t smem_cols(const tsne_plan* pl) { return sizeof(float2) * 12 * pl->L_max; }
 static size_t smem_rows_inv(const tsne_plan* pl) { return sizeof(float2) * 4 * pl->L_max; }
 static size_t smem_1d(const tsne_plan* pl) { return sizeof(float2) * 4 * pl->L_max; }
 
@@ -446,7 +499,7 @@ cudaError_t fft_configure(tsne_plan* pl) {
 
 cudaError_t launch_convolution(tsne_plan* pl, double* Z_out) {
     if (pl->s == 2) {
-        const int g1 = (int)std::min<int64_t>(3 * (int64_t)pl->n_max, 4 * pl->sm_count);
+        const int g1 = (int)std::min<int64_t>(4 * (int64_t)pl->n_max, 4 * pl->sm_count);
         rows_fwd_kernel<<<g1, 256, smem_rows_fwd(pl), pl->stream>>>(pl->w, pl->params, pl->fft_table,
                                                                      pl->twiddles, pl->spec);
         const int g2 = (int)std::min<int64_t>(pl->L_max / 2 + 1, 2 * pl->sm_count);

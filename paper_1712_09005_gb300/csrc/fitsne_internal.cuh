@@ -37,7 +37,7 @@ struct Params {
     float delta;      // node spacing b / p
     float inv_delta;  // p / b
     float delta2;     // delta^2 (kernel argument scale)
-    float centre;     // y_min + width / 2, subtracted from the y charges
+    float fx_scale;   // 2^fx_shift: spread values are accumulated as integers x * fx_scale
     int32_t n_int;    // intervals per dimension
     int32_t n;        // nodes per dimension = p * n_int
     int32_t L;        // FFT length per dimension (even, >= 2n)
@@ -45,10 +45,10 @@ struct Params {
     int32_t fft_idx;  // entry of the FFT table
     int32_t n_chunks; // spread work items
     int32_t error;    // latched TSNE_ERR_NONFINITE
-    int32_t pad;
+    int32_t fx_shift; // binary point of the fixed-point spread grids
     double Z;         // sum_i h_1(y_i) - N
     float inv_Z;      // 1 / Z in FP32
-    float pad2;
+    float fx_inv;     // 2^-fx_shift
 };
 
 }  // namespace fitsne
@@ -72,6 +72,7 @@ struct tsne_plan {
     int force_box;
     float force_y_min, force_width;
     int force_n_int;
+    int fx_shift;            // fixed-point binary point of the spread (plan constant)
     // device memory
     fitsne::Params* params;
     float* box_partial;      // [kBoxBlocks * 2] min/max per block
@@ -84,8 +85,8 @@ struct tsne_plan {
     int32_t* block_pts;      // [scan_blocks] per-block totals then offsets
     int32_t* block_chunks;   // [scan_blocks]
     float* sorted_y;         // [N * s] coordinates grouped by box
-    float* w;                // [(s+1) * n_max^s] spread grids
-    float2* spec;            // [3 * n_max * L_max] row spectra (s = 2)
+    long long* w;            // [(s+1) * n_max^s] spread grids, fixed point 2^-fx_shift
+    float2* spec;            // [4 * n_max * L_max] row spectra (s = 2)
     float4* hgrid;           // [n_max^s] node potentials
     double* z_partial;       // [n_max]
     double* kl_partial;      // [kl_blocks]

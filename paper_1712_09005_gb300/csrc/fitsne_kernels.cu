@@ -34,19 +34,20 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // Reduces a[0..NV) (NV a multiple of 32) across the warp so that, for every
 // group g of 32 values, lane l ends with the warp total of value g*32 + l in
-// a[g*32]. 31 shuffles per group instead of 5 per value.
-template <int NV>
-__device__ __forceinline__ void warp_transpose_reduce(float (&a)[NV], int lane) {
+// a[g*32]. 31 shuffles per group instead of 5 per value. Integer T makes the
+// result independent of the order of the additions.
+template <int NV, typename T>
+__device__ __forceinline__ void warp_transpose_reduce(T (&a)[NV], int lane) {
 #pragma unroll
     for (int g = 0; g < NV / 32; ++g) {
-        float* v = a + g * 32;
+        T* v = a + g * 32;
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
             const bool upper = (lane & off) != 0;
 #pragma unroll
             for (int i = 0; i < off; ++i) {
-                float send = upper ? v[i] : v[i + off];
-                float keep = upper ? v[i + off] : v[i];
+                T send = upper ? v[i] : v[i + off];
+                T keep = upper ? v[i + off] : v[i];
                 v[i] = keep + __shfl_xor_sync(kFull, send, off);
             }
         }
@@ -72,7 +73,7 @@ __device__ __forceinline__ int box_of(const float* __restrict__ Y, int64_t i, co
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBoxThreads)
 box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_fixed, int n_min,
-           int n_int_max, int force, float f_y_min, float f_width, int f_n_int,
+           int n_int_max, int force, float f_y_min, float f_width, int f_n_int, int fx_shift,
            float* __restrict__ partial, unsigned* __restrict__ ticket, Params* __restrict__ params,
            const FftEntry* __restrict__ table, int n_fft) {
     float lo = INFINITY, hi = -INFINITY;
@@ -164,7 +165,9 @@ box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_f
     P.delta = __fdiv_rn(P.b, (float)p);
     P.inv_delta = __fdiv_rn((float)p, P.b);
     P.delta2 = __fmul_rn(P.delta, P.delta);
-    P.centre = __fadd_rn(y_min, __fmul_rn(0.5f, width));
+    P.fx_shift = fx_shift;
+    P.fx_scale = ldexpf(1.0f, fx_shift);
+    P.fx_inv = ldexpf(1.0f, -fx_shift);
     P.n = p * n_int;
     P.n_boxes = (s == 2) ? n_int * n_int : n_int;
     int idx = n_fft - 1;
@@ -174,10 +177,8 @@ box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_f
     P.fft_idx = idx;
     P.L = table[idx].L;
     P.n_chunks = 0;
-    P.pad = 0;
     P.Z = 0.0;
     P.inv_Z = 0.0f;
-    P.pad2 = 0.0f;
     *params = P;
 }
 
@@ -313,7 +314,7 @@ scan_boxes_kernel(int32_t* __restrict__ counts, const Params* __restrict__ param
                   const int32_t* __restrict__ block_pts, const int32_t* __restrict__ block_chunks,
                   int32_t* __restrict__ box_start, int32_t* __restrict__ cursor,
                   int32_t* __restrict__ chunk_start, int32_t* __restrict__ chunk_box,
-                  float* __restrict__ w, int64_t N) {
+                  long long* __restrict__ w, int64_t N) {
     __shared__ int sw[32];
     const Params P = *params;
     const int nb = P.n_boxes;
@@ -341,7 +342,7 @@ scan_boxes_kernel(int32_t* __restrict__ counts, const Params* __restrict__ param
                     for (int j2 = 0; j2 < (S == 2 ? PP : 1); ++j2) {
                         int64_t g = (S == 2) ? (int64_t)(bx * PP + j1) * n + (by * PP + j2)
                                              : (int64_t)(bx * PP + j1);
-                        w[ch * G + g] = 0.0f;
+                        w[ch * G + g] = 0;
                     }
             if (b == nb - 1) {
                 box_start[nb] = (int32_t)N;
@@ -355,15 +356,23 @@ scan_boxes_kernel(int32_t* __restrict__ counts, const Params* __restrict__ param
 
 // ----------------------------------------------------------------------------
 // Step 1 (spread): one warp per chunk of at most kChunk points of one box.
-// Each lane accumulates the (s+1) p^s node sums of its points in registers
-// (charges 1 and y(m) - centre); a transpose reduction gives lane v the warp
-// total of value v. Boxes with one chunk store; larger boxes add atomically.
+// For node g = (j1, j2) of the box and a point with local coordinates t
+// (units of delta), the point adds W = L_j1(t1) L_j2(t2) to the charge grid
+// w0 and W (t_m - j_m - 1/2) to the dipole grids d_m, the charge y(m) taken
+// relative to the node it lands on: sum_g L_g(y) (y(m) - y~_g(m)) / delta.
+// This equals the paper's spread of the charges y(m) less y~_g(m) w0[g]
+// (exact: spreading is linear in the charge), and keeps every value O(1).
+// Values are accumulated as 64-bit integers of x * 2^fx_shift, so the sums
+// (in registers, across lanes, and the atomics of boxes with several chunks)
+// do not depend on the order of the points: the grids are bitwise
+// reproducible. Each lane accumulates its points; a transpose reduction
+// gives lane v the warp total of value v.
 // ----------------------------------------------------------------------------
 template <int S, int PP>
 __global__ void __launch_bounds__(256)
 spread_kernel(const float* __restrict__ sorted_y, const int32_t* __restrict__ box_start,
               const int32_t* __restrict__ chunk_start, const int32_t* __restrict__ chunk_box,
-              const Params* __restrict__ params, float* __restrict__ w) {
+              const Params* __restrict__ params, long long* __restrict__ w) {
     constexpr int NODES = (S == 2) ? PP * PP : PP;
     constexpr int NVAL = (S + 1) * NODES;
     constexpr int NV = (NVAL + 31) / 32 * 32;
@@ -373,6 +382,7 @@ spread_kernel(const float* __restrict__ sorted_y, const int32_t* __restrict__ bo
     const int nwarp = gridDim.x * blockDim.x / 32;
     const int n = P.n;
     const int64_t G = (S == 2) ? (int64_t)n * n : n;
+    const float sc = P.fx_scale;
     for (int q = (blockIdx.x * blockDim.x + threadIdx.x) / 32; q < P.n_chunks; q += nwarp) {
         const int box = chunk_box[q];
         const int bs = box_start[box];
@@ -382,32 +392,36 @@ spread_kernel(const float* __restrict__ sorted_y, const int32_t* __restrict__ bo
         const int len = min(kChunk, cnt - ci * kChunk);
         const int bx = (S == 2) ? box / P.n_int : box;
         const int by = (S == 2) ? box % P.n_int : 0;
-        float acc[NV];
+        long long acc[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = 0.0f;
+        for (int v = 0; v < NV; ++v) acc[v] = 0;
         for (int k = lane; k < len; k += 32) {
-            float L1[PP], L2[PP];
-            float q1, q2 = 0.0f;
+            float L1[PP], L2[PP], e1[PP], e2[PP];
             if (S == 2) {
-                float2 y = reinterpret_cast<const float2*>(sorted_y)[start + k];
-                lagrange<PP>(local_t(y.x, bx, P), L1);
-                lagrange<PP>(local_t(y.y, by, P), L2);
-                q1 = y.x - P.centre;
-                q2 = y.y - P.centre;
+                const float2 y = reinterpret_cast<const float2*>(sorted_y)[start + k];
+                const float t1 = local_t(y.x, bx, P), t2 = local_t(y.y, by, P);
+                lagrange<PP>(t1, L1);
+                lagrange<PP>(t2, L2);
+#pragma unroll
+                for (int j = 0; j < PP; ++j) {
+                    e1[j] = t1 - ((float)j + 0.5f);
+                    e2[j] = t2 - ((float)j + 0.5f);
+                }
             } else {
-                float y = sorted_y[start + k];
-                lagrange<PP>(local_t(y, bx, P), L1);
-                q1 = y - P.centre;
+                const float t1 = local_t(sorted_y[start + k], bx, P);
+                lagrange<PP>(t1, L1);
+#pragma unroll
+                for (int j = 0; j < PP; ++j) e1[j] = t1 - ((float)j + 0.5f);
             }
 #pragma unroll
             for (int j1 = 0; j1 < PP; ++j1) {
 #pragma unroll
                 for (int j2 = 0; j2 < (S == 2 ? PP : 1); ++j2) {
-                    const float wt = (S == 2) ? L1[j1] * L2[j2] : L1[j1];
+                    const float W = (S == 2) ? L1[j1] * L2[j2] : L1[j1];
                     const int node = (S == 2) ? j1 * PP + j2 : j1;
-                    acc[node] += wt;
-                    acc[NODES + node] += wt * q1;
-                    if (S == 2) acc[2 * NODES + node] += wt * q2;
+                    acc[node] += __float2ll_rn(W * sc);
+                    acc[NODES + node] += __float2ll_rn((W * e1[j1]) * sc);
+                    if (S == 2) acc[2 * NODES + node] += __float2ll_rn((W * e2[j2]) * sc);
                 }
             }
         }
@@ -422,9 +436,12 @@ spread_kernel(const float* __restrict__ sorted_y, const int32_t* __restrict__ bo
                 const int j2 = (S == 2) ? node % PP : 0;
                 const int64_t gi = (S == 2) ? (int64_t)(bx * PP + j1) * n + (by * PP + j2)
                                             : (int64_t)(bx * PP + j1);
-                float* dst = &w[ch * G + gi];
-                if (multi) atomicAdd(dst, acc[g * 32]);
-                else *dst = acc[g * 32];
+                long long* dst = &w[ch * G + gi];
+                if (multi)
+                    atomicAdd(reinterpret_cast<unsigned long long*>(dst),
+                              static_cast<unsigned long long>(acc[g * 32]));
+                else
+                    *dst = acc[g * 32];
             }
         }
     }
@@ -433,11 +450,15 @@ spread_kernel(const float* __restrict__ sorted_y, const int32_t* __restrict__ bo
 // ----------------------------------------------------------------------------
 // Attraction + Step 3 + gradient (+ update). One warp per CSR row i:
 //   A_i = sum_j p_ij (y_i - y_j) / (1 + |y_i - y_j|^2)                 (Sec. 3)
-//   h_k(y_i) = sum over the p^s nodes of y_i's box of L(y_i) v_k[node] (Step 3)
-//   F_rep,i(m) = (h_{m+1} - (y_i(m) - c) h_{s+2}) / Z                  (Appendix)
+//   F_rep,i(m) = (h_{m+1}(y_i) - y_i(m) h_{s+2}(y_i)) / Z              (Appendix)
 //   dY_i = 4 (alpha A_i + F_rep,i)                                     (Sec. 1.2)
-// The h values carry the centred charges y - c, so y_i(m) - c multiplies
-// h_{s+2}; its rounding error is carried along exactly (two-sum).
+// with the interpolated h of Step 3. The numerator is evaluated in the
+// node-relative form: with u_m = v_m - y~(m) v_{s+2} at each node (computed
+// by the convolution without cancellation, see fitsne_fft.cu),
+//   h_{m+1}(y_i) - y_i(m) h_{s+2}(y_i)
+//     = sum_g L_g(y_i) [u_m[g] + (y~_g(m) - y_i(m)) v_{s+2}[g]]
+//     = delta sum_g L_g(y_i) [u'_m[g] + (j_m + 1/2 - t_m) v_{s+2}[g]],
+// an identity in exact arithmetic whose terms stay O(1) in FP32.
 // ----------------------------------------------------------------------------
 struct StepArgs {
     float* Y_new;
@@ -525,56 +546,48 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
         a0 = warp_sum(a0);
         if (S == 2) a1 = warp_sum(a1);
 
-        // Step 3: interpolate the node potentials of y_i's box
+        // Step 3: interpolate the node values of y_i's box
         const int l1 = interval_of(yi0, P);
         const int l2 = (S == 2) ? interval_of(yi1, P) : 0;
-        float r1 = 0.0f, r2 = 0.0f, r3 = 0.0f;
+        float r1 = 0.0f, r2 = 0.0f;
         if (node_lane) {
             float L1[PP];
-            lagrange<PP>(local_t(yi0, l1, P), L1);
+            const float t1 = local_t(yi0, l1, P);
+            lagrange<PP>(t1, L1);
             float w1 = 0.0f;
 #pragma unroll
             for (int k = 0; k < PP; ++k) if (k == j1) w1 = L1[k];
             float wt = w1;
             int64_t gi;
+            float o2 = 0.0f;
             if (S == 2) {
                 float L2[PP];
-                lagrange<PP>(local_t(yi1, l2, P), L2);
+                const float t2 = local_t(yi1, l2, P);
+                lagrange<PP>(t2, L2);
                 float w2 = 0.0f;
 #pragma unroll
                 for (int k = 0; k < PP; ++k) if (k == j2) w2 = L2[k];
                 wt = w1 * w2;
                 gi = (int64_t)(l1 * PP + j1) * n + (l2 * PP + j2);
+                o2 = ((float)j2 + 0.5f) - t2;
             } else {
                 gi = l1 * PP + j1;
             }
-            const float4 h = __ldg(&hgrid[gi]);
-            r1 = wt * h.y;
-            r2 = wt * h.z;
-            r3 = wt * h.w;
+            const float o1 = ((float)j1 + 0.5f) - t1;
+            const float4 h = __ldg(&hgrid[gi]);  // (h1, u'1, u'2, v_{s+2})
+            r1 = wt * __fmaf_rn(o1, h.w, h.y);
+            if (S == 2) r2 = wt * __fmaf_rn(o2, h.w, h.z);
         }
 #pragma unroll
         for (int o = (NODES > 16 ? 16 : (NODES > 8 ? 8 : (NODES > 4 ? 4 : (NODES > 2 ? 2 : 1))));
              o >= 1; o >>= 1) {
             r1 += __shfl_xor_sync(kFull, r1, o);
             if (S == 2) r2 += __shfl_xor_sync(kFull, r2, o);
-            r3 += __shfl_xor_sync(kFull, r3, o);
         }
         if (lane == 0) {
-        // Appendix: F_rep(m) = (h_{m+1} - (y(m) - c) h_{s+2}) / Z
-        float c_hi = yi0 - P.centre;
-        float bb = c_hi - yi0;
-        float c_lo = (yi0 - (c_hi - bb)) + (-P.centre - bb);
-        const float f0 = (__fmaf_rn(-c_hi, r3, r1) - c_lo * r3) * invZ;
-        const float g0 = 4.0f * (alpha * a0 + f0);
-        float g1 = 0.0f;
-        if (S == 2) {
-            float d_hi = yi1 - P.centre;
-            float b2 = d_hi - yi1;
-            float d_lo = (yi1 - (d_hi - b2)) + (-P.centre - b2);
-            const float f1 = (__fmaf_rn(-d_hi, r3, r2) - d_lo * r3) * invZ;
-            g1 = 4.0f * (alpha * a1 + f1);
-        }
+        const float fs = P.delta * invZ;
+        const float g0 = 4.0f * (alpha * a0 + r1 * fs);
+        const float g1 = (S == 2) ? 4.0f * (alpha * a1 + r2 * fs) : 0.0f;
         if (!STEP) {
             if (S == 2) reinterpret_cast<float2*>(dY)[i] = make_float2(g0, g1);
             else dY[i] = g0;
@@ -706,7 +719,8 @@ static int grid_for(const tsne_plan* pl, int64_t items, int per_block, int per_s
 cudaError_t launch_box(tsne_plan* pl, const float* Y) {
     box_kernel<<<kBoxBlocks, kBoxThreads, 0, pl->stream>>>(
         Y, pl->N * pl->s, pl->s, pl->p, pl->n_int_fixed, pl->n_min, pl->n_int_max, pl->force_box,
-        pl->force_y_min, pl->force_width, pl->force_n_int, pl->box_partial, pl->tickets + 0,
+        pl->force_y_min, pl->force_width, pl->force_n_int, pl->fx_shift, pl->box_partial,
+        pl->tickets + 0,
         pl->params, pl->fft_table, pl->n_fft);
     pl->launches += 1;
     return cudaGetLastError();
