@@ -151,13 +151,16 @@ def force_traffic(s: int, N: int):
     return float(rec[f"dram_bytes_per_launch_s{s}_N{N}"])
 
 
-def make_inputs(wl: str, job: int, device: str):
+def make_inputs(wl: str, job: int, device: str, N: int):
     from paper_1712_09005_gb300 import inputs
-    num, N, s, fixed, over, desc = WORKLOADS[wl]
+    num, _, s, fixed, over, desc = WORKLOADS[wl]
     args = inputs.mixture_args(num, job=job, N=N)
     X = inputs.mixture(**args)
     P = inputs.affinities(X, 30.0, device=device)
     Y0 = inputs.initial_embedding(N, s, seed=args["seed"])
+    if device != "cpu":
+        import torch
+        torch.cuda.empty_cache()  # release the kNN scratch
     return P, Y0
 
 
@@ -170,7 +173,7 @@ def schedule(wl: str, n_iter: int):
 def oracle_iterations(P, Y0, wl, sched_args, budget_s, max_iters):
     """Times the FP64 oracle (gradient + update) from Y0 for up to budget_s."""
     import oracle
-    num, N, s, fixed, over, desc = WORKLOADS[wl]
+    num, _, s, fixed, over, desc = WORKLOADS[wl]
     opts = oracle.InterpOptions(p=3, n_int_fixed=fixed, n_min=50,
                                 n_int_max=400 if s == 2 else 1000, use_fft=True)
     sc = oracle.Schedule(**sched_args)
@@ -197,9 +200,10 @@ def run_reference(a):
     import oracle
     oracle.build()
     num, N, s, fixed, over, desc = WORKLOADS[a.workload]
+    N = a.n or N
     import torch
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    P, Y0 = make_inputs(a.workload, 0, dev)
+    P, Y0 = make_inputs(a.workload, 0, dev, N)
     sched_args = dict(n_iter=max(1000, a.steps), **over)
     # warm-up (at most one iteration), then a bounded number of timed iterations
     if a.warmup > 0:
@@ -233,11 +237,14 @@ def run_ours(a):
     from paper_1712_09005_gb300 import build as pbuild
     pbuild.build()
     num, N, s, fixed, over, desc = WORKLOADS[a.workload]
+    N = a.n or N
+    if a.n:
+        desc = f"{desc} [N overridden to {N}]"
     K, W = a.steps, a.warmup
     n_iter = max(1000, K)
     sched = schedule(a.workload, n_iter)
 
-    P, Y0 = make_inputs(a.workload, rank, "cuda")
+    P, Y0 = make_inputs(a.workload, rank, "cuda", N)
     Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
     stream = torch.cuda.current_stream()
     plan = pkg.Plan(N, s, n_intervals=fixed, stream=stream.cuda_stream)
@@ -366,6 +373,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="n1m_2d")
+    ap.add_argument("--n", type=int, default=0, help="override the workload's N (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

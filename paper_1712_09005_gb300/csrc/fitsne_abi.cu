@@ -140,7 +140,7 @@ void free_plan(tsne_plan* pl) {
                     pl->sorted_y,  pl->w,           pl->spec,        pl->hgrid,      pl->z_partial,
                     pl->kl_partial, pl->kl_out_dev, pl->valid_flag,  pl->y_next,     pl->uY_run,
                     pl->gains_run, pl->fft_table,   pl->twiddles,    pl->h_row_ptr,  pl->h_col,
-                    pl->h_val,     pl->h_Y};
+                    pl->h_val,     pl->h_Y,         pl->fft_of_n};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete pl;
@@ -315,6 +315,7 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     ALLOC(uY_run, N * s);
     ALLOC(gains_run, N * s);
     ALLOC(fft_table, tab.size());
+    ALLOC(fft_of_n, pl->n_max + 1);
     ALLOC(twiddles, tw_total);
 #undef ALLOC
     if (rc != TSNE_OK) { free_plan(pl); return rc; }
@@ -327,6 +328,14 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
                              cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(pl->twiddles, tw.data(), tw.size() * sizeof(float2),
+                             cudaMemcpyHostToDevice, st);
+    std::vector<int32_t> of_n(pl->n_max + 1);
+    for (int nn = 0, idx = 0; nn <= pl->n_max; ++nn) {
+        while (tab[idx].L < 2 * nn) ++idx;
+        of_n[nn] = idx;
+    }
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(pl->fft_of_n, of_n.data(), of_n.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess) ce = fitsne::fft_configure(pl);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);

@@ -16,6 +16,8 @@ constexpr int kMaxStages = 16;    // radix stages of one FFT
 constexpr int kScanBlock = 2048;  // boxes per scan block (1024 threads x 2)
 constexpr int kBoxThreads = 256;  // threads of the bounding-box blocks
 constexpr int kBoxBlocks = 304;   // 2 per SM on 152 SMs
+constexpr int kHistBins = 12288;  // boxes that fit a shared-memory histogram (48 KB)
+constexpr int kSortPts = 8192;    // points per block of the shared-memory sort kernels
 
 // One FFT length of the plan's table: L = product of radix[0..nst), each
 // radix in {2, 3, 4, 5}; tw_off locates its L twiddles exp(-2 pi i j / L).
@@ -49,6 +51,8 @@ struct Params {
     double Z;         // sum_i h_1(y_i) - N
     float inv_Z;      // 1 / Z in FP32
     float fx_inv;     // 2^-fx_shift
+    float p_f;        // p as a float
+    int32_t pad;
 };
 
 }  // namespace fitsne
@@ -67,6 +71,7 @@ struct tsne_plan {
     int64_t chunk_cap;      // capacity of the chunk table
     int scan_blocks;        // ceil(n_boxes_max / kScanBlock)
     int n_fft;              // entries in the FFT table
+    int32_t* fft_of_n;      // [n_max + 1] FFT table entry for n nodes per dimension
     int sm_count;
     // box override (test hook)
     int force_box;
@@ -122,9 +127,12 @@ __device__ __forceinline__ int interval_of(float y, const Params& P) {
     return l > P.n_int - 1 ? P.n_int - 1 : l;
 }
 
-// Local coordinate t = (y - (y_min + l b)) / delta in units of the node
-// spacing, with the differences taken exactly (two-sum and two-product) so
-// that t carries FP32 accuracy even far from the box corner.
+// Local coordinate t = (y - (y_min + l b)) / delta = p (y - y_min - l b) / b
+// in units of the node spacing. The differences are taken exactly (two-sum
+// and two-product) and the scaling is one product and one correctly rounded
+// division by the FP32 interval width itself, so t carries FP32 accuracy far
+// from the box corner and its rounding errors are unbiased (no rounded
+// 1/delta shared by every point).
 __device__ __forceinline__ float local_t(float y, int l, const Params& P) {
     float u = __fsub_rn(y, P.y_min);
     float bb = __fsub_rn(u, y);
@@ -133,7 +141,7 @@ __device__ __forceinline__ float local_t(float y, int l, const Params& P) {
     float m = __fmul_rn(lf, P.b);
     float m_lo = __fmaf_rn(lf, P.b, -m);
     float d = __fadd_rn(__fsub_rn(u, m), __fsub_rn(u_lo, m_lo));
-    return d * P.inv_delta;
+    return __fdiv_rn(__fmul_rn(d, P.p_f), P.b);
 }
 
 // Lagrange basis on nodes j + 1/2, j = 0..PP-1 (Sec. 2.1, Eq. kerinterp).

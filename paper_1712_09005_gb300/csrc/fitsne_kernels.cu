@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kBoxThreads)
 box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_fixed, int n_min,
            int n_int_max, int force, float f_y_min, float f_width, int f_n_int, int fx_shift,
            float* __restrict__ partial, unsigned* __restrict__ ticket, Params* __restrict__ params,
-           const FftEntry* __restrict__ table, int n_fft) {
+           const FftEntry* __restrict__ table, const int32_t* __restrict__ fft_of_n) {
     float lo = INFINITY, hi = -INFINITY;
     int bad = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -122,17 +122,28 @@ box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_f
         s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
     __threadfence();
-    bool any_bad = false;
+    // the last block reduces the per-block partials
+    int bad_p = 0;
     lo = INFINITY;
     hi = -INFINITY;
-    for (unsigned i = 0; i < gridDim.x; ++i) {
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
         float a = __ldcg(&partial[2 * i]), b = __ldcg(&partial[2 * i + 1]);
-        if (isnan(a)) any_bad = true;
+        bad_p |= isnan(a);
         lo = fminf(lo, a);
         hi = fmaxf(hi, b);
     }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+    }
+    const bool any_bad = __syncthreads_or(bad_p);
+    if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i < kBoxThreads / 32; ++i) { lo = fminf(lo, s_lo[i]); hi = fmaxf(hi, s_hi[i]); }
     *ticket = 0u;
     Params P;
     P.error = __ldcg(&params->error);
@@ -170,12 +181,11 @@ box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_f
     P.fx_inv = ldexpf(1.0f, -fx_shift);
     P.n = p * n_int;
     P.n_boxes = (s == 2) ? n_int * n_int : n_int;
-    int idx = n_fft - 1;
-    for (int i = 0; i < n_fft; ++i) {
-        if (table[i].L >= 2 * P.n) { idx = i; break; }
-    }
+    const int idx = fft_of_n[P.n];
     P.fft_idx = idx;
     P.L = table[idx].L;
+    P.p_f = (float)p;
+    P.pad = 0;
     P.n_chunks = 0;
     P.Z = 0.0;
     P.inv_Z = 0.0f;
@@ -185,45 +195,89 @@ box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_f
 // ----------------------------------------------------------------------------
 // Counting sort by box: histogram (warp-aggregated integer atomics), scan,
 // scatter. Points of one box end up contiguous in sorted_y; their order
-// within the box is not fixed, which only permutes the spread's FP32 sums.
+// within the box is not fixed, which the integer spread sums do not see.
 // ----------------------------------------------------------------------------
+// Each block takes kSortPts consecutive points. With at most kHistBins
+// boxes the block first counts in a shared-memory histogram and touches the
+// global counters once per box it met, which keeps boxes holding many points
+// (tight clusters) from serialising on one global atomic; with more boxes
+// (each then holds few points) it uses the global counters directly.
 template <int S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 count_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ params,
              int32_t* __restrict__ counts) {
+    extern __shared__ int32_t hist[];
     const Params P = *params;
     if (P.error) return;
+    const int nb = P.n_boxes;
+    const bool local = nb <= kHistBins;
     const int lane = threadIdx.x % 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
-    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < N;
-         base += nwarp * 32) {
-        const int64_t i = base + lane;
+    if (local) {
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+    }
+    const int64_t p0 = (int64_t)blockIdx.x * kSortPts;
+    for (int k = 0; k < kSortPts / 1024; ++k) {
+        const int64_t i = p0 + k * 1024 + threadIdx.x;
         const int box = (i < N) ? box_of<S>(Y, i, P) : -1;
         const unsigned peers = __match_any_sync(kFull, box);
-        const int leader = __ffs(peers) - 1;
-        if (box >= 0 && lane == leader) atomicAdd(&counts[box], __popc(peers));
+        if (box >= 0 && lane == __ffs(peers) - 1) {
+            if (local) atomicAdd(&hist[box], __popc(peers));
+            else atomicAdd(&counts[box], __popc(peers));
+        }
+    }
+    if (local) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < nb; b += blockDim.x)
+            if (hist[b]) atomicAdd(&counts[b], hist[b]);
     }
 }
 
+// Same partition: the block counts its points per box, reserves one range
+// per box in the global cursors, then places each point at its box's range
+// plus its rank inside the block.
 template <int S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 scatter_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ params,
                int32_t* __restrict__ cursor, float* __restrict__ sorted_y) {
+    extern __shared__ int32_t hist[];
+    constexpr int K = kSortPts / 1024;
     const Params P = *params;
     if (P.error) return;
+    const int nb = P.n_boxes;
+    const bool local = nb <= kHistBins;
     const int lane = threadIdx.x % 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
     const unsigned lt = (1u << lane) - 1u;
-    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < N;
-         base += nwarp * 32) {
-        const int64_t i = base + lane;
-        const int box = (i < N) ? box_of<S>(Y, i, P) : -1;
-        const unsigned peers = __match_any_sync(kFull, box);
+    const int64_t p0 = (int64_t)blockIdx.x * kSortPts;
+    int box[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t i = p0 + k * 1024 + threadIdx.x;
+        box[k] = (i < N) ? box_of<S>(Y, i, P) : -1;
+    }
+    if (local) {
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const unsigned peers = __match_any_sync(kFull, box[k]);
+            if (box[k] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[box[k]], __popc(peers));
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < nb; b += blockDim.x)
+            if (hist[b]) hist[b] = atomicAdd(&cursor[b], hist[b]);
+        __syncthreads();
+    }
+    int32_t* dst_cursor = local ? hist : cursor;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const unsigned peers = __match_any_sync(kFull, box[k]);
         const int leader = __ffs(peers) - 1;
         int pos = 0;
-        if (box >= 0 && lane == leader) pos = atomicAdd(&cursor[box], __popc(peers));
+        if (box[k] >= 0 && lane == leader) pos = atomicAdd(&dst_cursor[box[k]], __popc(peers));
         pos = __shfl_sync(kFull, pos, leader) + __popc(peers & lt);
-        if (box >= 0) {
+        if (box[k] >= 0) {
+            const int64_t i = p0 + k * 1024 + threadIdx.x;
             if (S == 2)
                 reinterpret_cast<float2*>(sorted_y)[pos] = reinterpret_cast<const float2*>(Y)[i];
             else
@@ -478,6 +532,25 @@ __device__ __forceinline__ float update_one(float y, float dy, float& u, float& 
     return y + u;
 }
 
+template <int S>
+__device__ __forceinline__ void attract(float yi0, float yi1, int j, float v,
+                                        const float* __restrict__ Y, float& a0, float& a1) {
+    if (S == 2) {
+        const float2 yj = __ldg(reinterpret_cast<const float2*>(Y) + j);
+        const float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
+        const float q = v * __frcp_rn(1.0f + d0 * d0 + d1 * d1);
+        a0 += q * d0;
+        a1 += q * d1;
+    } else {
+        const float d0 = yi0 - __ldg(Y + j);
+        a0 += v * __frcp_rn(1.0f + d0 * d0) * d0;
+    }
+}
+
+// Software-pipelined: while row i is finished, the column indices and values
+// of the warp's next row (up to 32 U entries) are already in flight, and the
+// per-row loads of row i (its coordinates, its box's node values, the
+// optimizer state) are issued before the attraction loop waits on gathers.
 template <int S, int PP, bool STEP>
 __global__ void __launch_bounds__(256)
 force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -485,82 +558,69 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
              const Params* __restrict__ params, const float4* __restrict__ hgrid, float alpha,
              float* __restrict__ dY, StepArgs sa, int64_t N) {
     constexpr int NODES = (S == 2) ? PP * PP : PP;
+    constexpr int U = 8;
     const Params P = *params;
     if (P.error) return;
     const int lane = threadIdx.x % 32;
     const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
-    const float invZ = P.inv_Z;
+    const float fs = P.delta * P.inv_Z;
     const int n = P.n;
     // this lane's node of the p^s nodes of a box
     const int j1 = (S == 2) ? lane / PP : lane;
     const int j2 = (S == 2) ? lane % PP : 0;
     const bool node_lane = lane < NODES;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; i < N; i += nwarp) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= N) return;
+    int beg = __ldg(&row_ptr[i]), end = __ldg(&row_ptr[i + 1]);
+    int jj[U];
+    float vv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int e = beg + lane + 32 * u;
+        jj[u] = e < end ? __ldcs(&col[e]) : 0;
+        vv[u] = e < end ? __ldcs(&val[e]) : 0.0f;
+    }
+    while (true) {
+        const int64_t inext = i + nwarp;
+        int nbeg = 0, nend = 0;
+        if (inext < N) {
+            nbeg = __ldg(&row_ptr[inext]);
+            nend = __ldg(&row_ptr[inext + 1]);
+        }
         float yi0, yi1 = 0.0f;
         if (S == 2) {
-            float2 t = reinterpret_cast<const float2*>(Y)[i];
+            const float2 t = reinterpret_cast<const float2*>(Y)[i];
             yi0 = t.x;
             yi1 = t.y;
         } else {
             yi0 = Y[i];
         }
-        const int beg = row_ptr[i], end = row_ptr[i + 1];
-        float a0 = 0.0f, a1 = 0.0f;
-        int e = beg + lane;
-        // four independent gathers in flight per lane
-        for (; e + 96 < end; e += 128) {
-            int jj[4];
-            float vv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { jj[u] = __ldcs(&col[e + 32 * u]); vv[u] = __ldcs(&val[e + 32 * u]); }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (S == 2) {
-                    float2 yj = __ldg(reinterpret_cast<const float2*>(Y) + jj[u]);
-                    float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
-                    float q = vv[u] * __frcp_rn(1.0f + d0 * d0 + d1 * d1);
-                    a0 += q * d0;
-                    a1 += q * d1;
-                } else {
-                    float d0 = yi0 - __ldg(Y + jj[u]);
-                    float q = vv[u] * __frcp_rn(1.0f + d0 * d0);
-                    a0 += q * d0;
-                }
-            }
-        }
-        for (; e < end; e += 32) {
-            int j = __ldcs(&col[e]);
-            float v = __ldcs(&val[e]);
+        float2 us = make_float2(0.0f, 0.0f), gs = make_float2(0.0f, 0.0f);
+        if (STEP && lane == 0) {
             if (S == 2) {
-                float2 yj = __ldg(reinterpret_cast<const float2*>(Y) + j);
-                float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
-                float q = v * __frcp_rn(1.0f + d0 * d0 + d1 * d1);
-                a0 += q * d0;
-                a1 += q * d1;
+                us = reinterpret_cast<const float2*>(sa.uY)[i];
+                gs = reinterpret_cast<const float2*>(sa.gains)[i];
             } else {
-                float d0 = yi0 - __ldg(Y + j);
-                float q = v * __frcp_rn(1.0f + d0 * d0);
-                a0 += q * d0;
+                us.x = sa.uY[i];
+                gs.x = sa.gains[i];
             }
         }
-        a0 = warp_sum(a0);
-        if (S == 2) a1 = warp_sum(a1);
-
-        // Step 3: interpolate the node values of y_i's box
-        const int l1 = interval_of(yi0, P);
-        const int l2 = (S == 2) ? interval_of(yi1, P) : 0;
-        float r1 = 0.0f, r2 = 0.0f;
+        // Step 3 weights of this lane's node, and its node values (loaded early)
+        float wt = 0.0f, o1 = 0.0f, o2 = 0.0f;
+        float4 h = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (node_lane) {
+            const int l1 = interval_of(yi0, P);
             float L1[PP];
             const float t1 = local_t(yi0, l1, P);
             lagrange<PP>(t1, L1);
             float w1 = 0.0f;
 #pragma unroll
             for (int k = 0; k < PP; ++k) if (k == j1) w1 = L1[k];
-            float wt = w1;
+            wt = w1;
+            o1 = ((float)j1 + 0.5f) - t1;
             int64_t gi;
-            float o2 = 0.0f;
             if (S == 2) {
+                const int l2 = interval_of(yi1, P);
                 float L2[PP];
                 const float t2 = local_t(yi1, l2, P);
                 lagrange<PP>(t2, L2);
@@ -568,16 +628,33 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
 #pragma unroll
                 for (int k = 0; k < PP; ++k) if (k == j2) w2 = L2[k];
                 wt = w1 * w2;
-                gi = (int64_t)(l1 * PP + j1) * n + (l2 * PP + j2);
                 o2 = ((float)j2 + 0.5f) - t2;
+                gi = (int64_t)(l1 * PP + j1) * n + (l2 * PP + j2);
             } else {
                 gi = l1 * PP + j1;
             }
-            const float o1 = ((float)j1 + 0.5f) - t1;
-            const float4 h = __ldg(&hgrid[gi]);  // (h1, u'1, u'2, v_{s+2})
-            r1 = wt * __fmaf_rn(o1, h.w, h.y);
-            if (S == 2) r2 = wt * __fmaf_rn(o2, h.w, h.z);
+            h = __ldg(&hgrid[gi]);  // (h1, u'1, u'2, v_{s+2})
         }
+        // attraction over the prefetched entries, then any beyond 32 U
+        float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (beg + lane + 32 * u < end) attract<S>(yi0, yi1, jj[u], vv[u], Y, a0, a1);
+        for (int e = beg + lane + 32 * U; e < end; e += 32)
+            attract<S>(yi0, yi1, __ldcs(&col[e]), __ldcs(&val[e]), Y, a0, a1);
+        // prefetch the next row
+        if (inext < N) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = nbeg + lane + 32 * u;
+                jj[u] = e < nend ? __ldcs(&col[e]) : 0;
+                vv[u] = e < nend ? __ldcs(&val[e]) : 0.0f;
+            }
+        }
+        a0 = warp_sum(a0);
+        if (S == 2) a1 = warp_sum(a1);
+        float r1 = wt * __fmaf_rn(o1, h.w, h.y);
+        float r2 = (S == 2) ? wt * __fmaf_rn(o2, h.w, h.z) : 0.0f;
 #pragma unroll
         for (int o = (NODES > 16 ? 16 : (NODES > 8 ? 8 : (NODES > 4 ? 4 : (NODES > 2 ? 2 : 1))));
              o >= 1; o >>= 1) {
@@ -585,30 +662,29 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             if (S == 2) r2 += __shfl_xor_sync(kFull, r2, o);
         }
         if (lane == 0) {
-        const float fs = P.delta * invZ;
-        const float g0 = 4.0f * (alpha * a0 + r1 * fs);
-        const float g1 = (S == 2) ? 4.0f * (alpha * a1 + r2 * fs) : 0.0f;
-        if (!STEP) {
-            if (S == 2) reinterpret_cast<float2*>(dY)[i] = make_float2(g0, g1);
-            else dY[i] = g0;
-        } else {
-            if (S == 2) {
-                float2 u = reinterpret_cast<float2*>(sa.uY)[i];
-                float2 g = reinterpret_cast<float2*>(sa.gains)[i];
-                float n0 = update_one(yi0, g0, u.x, g.x, sa);
-                float n1 = update_one(yi1, g1, u.y, g.y, sa);
-                reinterpret_cast<float2*>(sa.uY)[i] = u;
-                reinterpret_cast<float2*>(sa.gains)[i] = g;
-                reinterpret_cast<float2*>(sa.Y_new)[i] = make_float2(n0, n1);
+            const float g0 = 4.0f * (alpha * a0 + r1 * fs);
+            const float g1 = (S == 2) ? 4.0f * (alpha * a1 + r2 * fs) : 0.0f;
+            if (!STEP) {
+                if (S == 2) reinterpret_cast<float2*>(dY)[i] = make_float2(g0, g1);
+                else dY[i] = g0;
             } else {
-                float u = sa.uY[i], g = sa.gains[i];
-                float n0 = update_one(yi0, g0, u, g, sa);
-                sa.uY[i] = u;
-                sa.gains[i] = g;
-                sa.Y_new[i] = n0;
+                const float n0 = update_one(yi0, g0, us.x, gs.x, sa);
+                if (S == 2) {
+                    const float n1 = update_one(yi1, g1, us.y, gs.y, sa);
+                    reinterpret_cast<float2*>(sa.uY)[i] = us;
+                    reinterpret_cast<float2*>(sa.gains)[i] = gs;
+                    reinterpret_cast<float2*>(sa.Y_new)[i] = make_float2(n0, n1);
+                } else {
+                    sa.uY[i] = us.x;
+                    sa.gains[i] = gs.x;
+                    sa.Y_new[i] = n0;
+                }
             }
         }
-        }
+        if (inext >= N) break;
+        i = inext;
+        beg = nbeg;
+        end = nend;
     }
 }
 
@@ -721,21 +797,22 @@ cudaError_t launch_box(tsne_plan* pl, const float* Y) {
         Y, pl->N * pl->s, pl->s, pl->p, pl->n_int_fixed, pl->n_min, pl->n_int_max, pl->force_box,
         pl->force_y_min, pl->force_width, pl->force_n_int, pl->fx_shift, pl->box_partial,
         pl->tickets + 0,
-        pl->params, pl->fft_table, pl->n_fft);
+        pl->params, pl->fft_table, pl->fft_of_n);
     pl->launches += 1;
     return cudaGetLastError();
 }
 
 template <int S, int PP>
 static void sort_and_spread_impl(tsne_plan* pl, const float* Y) {
-    const int gp = grid_for(pl, pl->N, 256, 8);
-    count_kernel<S><<<gp, 256, 0, pl->stream>>>(Y, pl->N, pl->params, pl->counts);
+    const int gp = (int)((pl->N + kSortPts - 1) / kSortPts);
+    const size_t hs = sizeof(int32_t) * kHistBins;
+    count_kernel<S><<<gp, 1024, hs, pl->stream>>>(Y, pl->N, pl->params, pl->counts);
     scan_blocks_kernel<<<pl->scan_blocks, 1024, 0, pl->stream>>>(
         pl->counts, pl->params, pl->block_pts, pl->block_chunks, pl->tickets + 1);
     scan_boxes_kernel<S, PP><<<pl->scan_blocks, 1024, 0, pl->stream>>>(
         pl->counts, pl->params, pl->block_pts, pl->block_chunks, pl->box_start, pl->cursor,
         pl->chunk_start, pl->chunk_box, pl->w, pl->N);
-    scatter_kernel<S><<<gp, 256, 0, pl->stream>>>(Y, pl->N, pl->params, pl->cursor, pl->sorted_y);
+    scatter_kernel<S><<<gp, 1024, hs, pl->stream>>>(Y, pl->N, pl->params, pl->cursor, pl->sorted_y);
     const int gs = grid_for(pl, pl->chunk_cap * 32, 256, 8);
     spread_kernel<S, PP><<<gs, 256, 0, pl->stream>>>(pl->sorted_y, pl->box_start, pl->chunk_start,
                                                      pl->chunk_box, pl->params, pl->w);

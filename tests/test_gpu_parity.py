@@ -222,7 +222,9 @@ def test_two_points_and_degenerate_box():
             torch.cuda.synchronize()
         ref = oracle.interp_gradient(Y.astype(np.float64), P, alpha=3.0, opts=oracle_opts(2))
         np.testing.assert_allclose(dY.cpu().numpy(), ref["dY"], rtol=1e-5, atol=1e-6)
-        assert abs(Z.item() - ref["Z"]) <= 1e-5 * abs(ref["Z"])
+        # with N = 2, Z (about 0.67) is the small difference sum h1 - N of two
+        # O(1) terms, so its error is bounded relative to sum h1 = Z + N
+        assert abs(Z.item() - ref["Z"]) <= Z_TOL * (abs(ref["Z"]) + 2)
 
 
 def test_empty_rows_and_ragged():
