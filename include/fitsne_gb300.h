@@ -223,10 +223,10 @@ int tsne_plan_info(tsne_plan* plan, tsne_plan_info_t* out);
  *   0  spread grids as FP64 [(s+1) x n^s] (accumulated exactly on the device
  *      in fixed point): w0 = sum_i L_g(y_i) and the dipole grids
  *      d_m = sum_i L_g(y_i) (t_m - j_m - 1/2) = (w_{y(m)} - y~_g(m) w0) / delta
- *   1  node values, fp32 [n^s x 4] = (h_1, u'_1, u'_2, v) with h_1 = K1 * w0,
- *      v = K2 * w0 (= h_{s+2} at the nodes), u'_m = K2 * d_m - G_m * w0 with
+ *   1  node values, fp32 [n^s x 4] = (0, u'_1, u'_2, v) with v = K2 * w0
+ *      (= h_{s+2} at the nodes) and u'_m = K2 * d_m - G_m * w0 with
  *      G_m(o) = o_m K2(o delta), i.e. (v_{m+1} - y~(m) v) / delta; u'_2 = 0
- *      when s = 1
+ *      when s = 1. (Z is formed from the spectra, so K1 * w0 is not kept.)
  *   2  bucket offsets, int32 [n_int^s + 1] (points per box, exclusive scan)
  * bytes must be at least the size above; the size needed is returned in
  * *bytes_needed (may be NULL).

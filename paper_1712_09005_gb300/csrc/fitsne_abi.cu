@@ -307,7 +307,7 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     ALLOC(w, (s + 1) * G);
     if (s == 2) ALLOC(spec, 4 * (int64_t)pl->n_max * pl->L_max);
     ALLOC(hgrid, G);
-    ALLOC(z_partial, pl->n_max);
+    ALLOC(z_partial, pl->L_max / 2 + 1);
     ALLOC(kl_partial, 2 * kl_blocks);
     ALLOC(kl_out_dev, 1);
     ALLOC(valid_flag, 1);

@@ -13,22 +13,24 @@
 // (exact). The transforms therefore produce, per node,
 //   (h1, u'_1, u'_2, v_{s+2}) = (K1 * w0, K2 * d_1 - G_1 * w0, K2 * d_2 - G_2 * w0, K2 * w0)
 // with u_m = delta u'_m; no output is a small difference of large values.
+// h1 is not formed: Z + N = sum_g w0[g] (K1 * w0)[g] = L^-s sum_k |W0^(k)|^2 K1^(k)
+// (Parseval; K1^ is real), summed in FP64 from the forward spectra.
 //
 // Real signals are packed in pairs into complex transforms:
 //   C0 = w0 + i d_1, C1 = d_2 (+ i 0), CK = K1 + i K2, CG = G_1 + i G_2.
 // K1, K2 are even in every offset (real, even spectra: Re / Im of one
 // transform); G_m is odd in offset m and even in the other (imaginary
 // spectrum i S_m), so the spectrum of CG is i S_1 - S_2. Outputs are packed
-// the same way: D0 = H1 + i U1 -> (h1, u'_1), D1 = U2 + i V -> (u'_2, v).
+// the same way: D0 = U1 + i U2 -> (u'_1, u'_2), D1 = V -> v.
 //
 // 2-D passes (one CTA per work item, grid-stride):
 //   rows_fwd_kernel  FFT along dimension 2 of the n rows of C0, C1, and of
 //                    the rows o1 = 0..n-1 of CK and CG (the rows o1 < 0
 //                    follow by symmetry)
 //   cols_kernel      per column pair (k2, L-k2): FFT along dimension 1,
-//                    split the packed spectra, multiply, pack, inverse FFT
-//   rows_inv_kernel  inverse FFT of the n needed rows, node values, and the
-//                    FP64 partial sums of Z = w0 . h1 - N
+//                    split the packed spectra, the Parseval sums of Z,
+//                    multiply, pack, inverse FFT
+//   rows_inv_kernel  inverse FFT of the n needed rows, node values
 // 1-D: conv1d_kernel does the whole convolution in one CTA.
 #include <math.h>
 
@@ -231,6 +233,28 @@ rows_fwd_kernel(const long long* __restrict__ w, const Params* __restrict__ para
     }
 }
 
+// Block sum of one double per thread (blockDim.x <= 1024); result in thread 0.
+__device__ __forceinline__ double block_sum_d(double v, double* sred) {
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    __syncthreads();
+    if (lane == 0) sred[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += sred[k];
+    return t;
+}
+
+// Publishes Z = sum_i h1(y_i) - N given S = sum_i h1(y_i) = w0 . (K1 * w0)
+// (equal: both are the sum of L_g(y_i) v1[g] over points and nodes).
+__device__ void publish_Z(double S, Params* params, double* Z_out, int64_t N) {
+    const double Z = S - (double)N;
+    params->Z = Z;
+    params->inv_Z = (float)(1.0 / Z);
+    if (Z_out) *Z_out = Z;
+}
+
 // ----------------------------------------------------------------------------
 // 2-D, pass 2: column pairs (k2, L - k2), k2 = 0 .. L/2. Forward FFT of six
 // columns (C0 and C1 at k2 and L - k2, CK and CG at k2), spectra products,
@@ -242,14 +266,19 @@ rows_fwd_kernel(const long long* __restrict__ w, const Params* __restrict__ para
 // -S_2(k1, k2) (G_2 is odd in o2).
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(512)
-cols_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ table,
-            const float2* __restrict__ tw_all, float2* __restrict__ spec) {
+cols_kernel(Params* params, const FftEntry* __restrict__ table,
+            const float2* __restrict__ tw_all, float2* __restrict__ spec,
+            double* __restrict__ z_partial, unsigned* __restrict__ ticket, double* Z_out,
+            int64_t N) {
     extern __shared__ float2 sm[];
     __shared__ FftEntry e;
+    __shared__ double sred[32];
+    __shared__ bool s_last;
     const Params P = *params;
-    if (P.error) return;
+    if (P.error) goto done;
     if (threadIdx.x == 0) e = table[P.fft_idx];
     __syncthreads();
+    {
     const int n = P.n, L = P.L;
     const float2* tw = tw_all + e.tw_off;
     float2* C0 = spec;
@@ -282,6 +311,7 @@ cols_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ tabl
         __syncthreads();
         float2* F = fft_batch(X, Yb, e, 6, tw, -1.0f);
         float2* O = (F == X) ? Yb : X;
+        double zp = 0.0;
         for (int k1 = threadIdx.x; k1 < L; k1 += blockDim.x) {
             const int k1n = (L - k1) % L;
             const float2 xa = F[k1], xb = F[L + k1];
@@ -297,18 +327,22 @@ cols_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ tabl
             const float2 ck = F[4 * L + k1];      // (K1^, K2^)
             const float2 cg = F[5 * L + k1];      // i S1 - S2
             const float K1 = ck.x, K2 = ck.y, S1 = cg.y, S2 = -cg.x;
-            // a: H1 = w0 K1, U1 = d1 K2 - i S1 w0, U2 = d2 K2 - i S2 w0, V = w0 K2
-            const float2 h1a = cscale(w0a, K1), va = cscale(w0a, K2);
+            // Parseval terms of Z + N at (k1, k2) and (k1, L - k2)
+            zp += ((double)w0a.x * w0a.x + (double)w0a.y * w0a.y) * (double)K1;
+            if (k2b != k2) zp += ((double)w0b.x * w0b.x + (double)w0b.y * w0b.y) * (double)K1;
+            // U1 = d1 K2 - i S1 w0, U2 = d2 K2 - i S2 w0, V = w0 K2 (S2 flips sign at L - k2)
+            const float2 va = cscale(w0a, K2), vb = cscale(w0b, K2);
             const float2 u1a = csub(cscale(d1a, K2), mul_si(w0a, S1));
             const float2 u2a = csub(cscale(d2a, K2), mul_si(w0a, S2));
-            const float2 h1b = cscale(w0b, K1), vb = cscale(w0b, K2);
             const float2 u1b = csub(cscale(d1b, K2), mul_si(w0b, S1));
             const float2 u2b = cadd(cscale(d2b, K2), mul_si(w0b, S2));
-            O[k1] = cadd(h1a, mul_si(u1a, 1.0f));
-            O[L + k1] = cadd(h1b, mul_si(u1b, 1.0f));
-            O[2 * L + k1] = cadd(u2a, mul_si(va, 1.0f));
-            O[3 * L + k1] = cadd(u2b, mul_si(vb, 1.0f));
+            O[k1] = cadd(u1a, mul_si(u2a, 1.0f));
+            O[L + k1] = cadd(u1b, mul_si(u2b, 1.0f));
+            O[2 * L + k1] = va;
+            O[3 * L + k1] = vb;
         }
+        const double zt = block_sum_d(zp, sred);
+        if (threadIdx.x == 0) z_partial[k2] = zt;
         __syncthreads();
         const float2* R = fft_batch(O, F, e, 4, tw, 1.0f);
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -321,77 +355,8 @@ cols_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ tabl
         }
         __syncthreads();
     }
-}
-
-// Block sum of one double per thread (blockDim.x <= 1024); result in thread 0.
-__device__ __forceinline__ double block_sum_d(double v, double* sred) {
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
-    __syncthreads();
-    if (lane == 0) sred[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += sred[k];
-    return t;
-}
-
-// Last block of a grid: sums the per-row partials in row order and publishes
-// Z = sum_i h1(y_i) - N = w_1 . h1 - N (the two agree: both equal the sum of
-// L_g(y_i) v1[g] over points and nodes).
-__device__ void publish_Z(const double* __restrict__ z_partial, int rows, Params* params,
-                          double* Z_out, int64_t N) {
-    double S = 0.0;
-    for (int r = 0; r < rows; ++r) S += __ldcg(&z_partial[r]);
-    const double Z = S - (double)N;
-    params->Z = Z;
-    params->inv_Z = (float)(1.0 / Z);
-    if (Z_out) *Z_out = Z;
-}
-
-// ----------------------------------------------------------------------------
-// 2-D, pass 3: inverse row FFTs of the first n rows of D0 and D1; node
-// values (h1, u'_1, u'_2, v) / L^2 for columns < n; FP64 row sums of w0 h1.
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-rows_inv_kernel(const long long* __restrict__ w, Params* params, const FftEntry* __restrict__ table,
-                const float2* __restrict__ tw_all, const float2* __restrict__ spec,
-                float4* __restrict__ hgrid, double* __restrict__ z_partial,
-                unsigned* __restrict__ ticket, double* Z_out, int64_t N) {
-    extern __shared__ float2 sm[];
-    __shared__ FftEntry e;
-    __shared__ double sred[32];
-    __shared__ bool s_last;
-    const Params P = *params;
-    const int n = P.n, L = P.L;
-    if (!P.error) {
-        if (threadIdx.x == 0) e = table[P.fft_idx];
-        __syncthreads();
-        const float2* tw = tw_all + e.tw_off;
-        const float2* D0 = spec;
-        const float2* D1 = spec + (int64_t)n * L;
-        float2* X = sm;
-        float2* Yb = sm + 2 * L;
-        const float scale = 1.0f / ((float)L * (float)L);
-        for (int r = blockIdx.x; r < n; r += gridDim.x) {
-            for (int c = threadIdx.x; c < L; c += blockDim.x) {
-                X[c] = D0[(int64_t)r * L + c];
-                X[L + c] = D1[(int64_t)r * L + c];
-            }
-            __syncthreads();
-            const float2* R = fft_batch(X, Yb, e, 2, tw, 1.0f);
-            double zp = 0.0;
-            for (int c = threadIdx.x; c < n; c += blockDim.x) {
-                const float2 a = R[c], b = R[L + c];
-                const float4 h = make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
-                hgrid[(int64_t)r * n + c] = h;
-                zp += (double)w[(int64_t)r * n + c] * (double)h.x;  // w0 in units of 2^-fx_shift
-            }
-            const double t = block_sum_d(zp, sred);
-            if (threadIdx.x == 0) z_partial[r] = t * (double)P.fx_inv;
-            __syncthreads();
-        }
     }
+done:
     if (threadIdx.x == 0) {
         __threadfence();
         s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
@@ -400,15 +365,56 @@ rows_inv_kernel(const long long* __restrict__ w, Params* params, const FftEntry*
     if (!s_last || threadIdx.x != 0) return;
     __threadfence();
     *ticket = 0u;
-    if (!P.error) publish_Z(z_partial, n, params, Z_out, N);
+    if (!P.error) {
+        double S = 0.0;
+        for (int k2 = 0; k2 <= P.L / 2; ++k2) S += __ldcg(&z_partial[k2]);
+        publish_Z(S / ((double)P.L * (double)P.L), params, Z_out, N);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// 2-D, pass 3: inverse row FFTs of the first n rows of D0 and D1; node
+// values (0, u'_1, u'_2, v) / L^2 for columns < n.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+rows_inv_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ table,
+                const float2* __restrict__ tw_all, const float2* __restrict__ spec,
+                float4* __restrict__ hgrid) {
+    extern __shared__ float2 sm[];
+    __shared__ FftEntry e;
+    const Params P = *params;
+    if (P.error) return;
+    const int n = P.n, L = P.L;
+    if (threadIdx.x == 0) e = table[P.fft_idx];
+    __syncthreads();
+    const float2* tw = tw_all + e.tw_off;
+    const float2* D0 = spec;
+    const float2* D1 = spec + (int64_t)n * L;
+    float2* X = sm;
+    float2* Yb = sm + 2 * L;
+    const float scale = 1.0f / ((float)L * (float)L);
+    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+            X[c] = D0[(int64_t)r * L + c];
+            X[L + c] = D1[(int64_t)r * L + c];
+        }
+        __syncthreads();
+        const float2* R = fft_batch(X, Yb, e, 2, tw, 1.0f);
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            const float2 a = R[c], b = R[L + c];
+            hgrid[(int64_t)r * n + c] = make_float4(0.0f, a.x * scale, a.y * scale, b.x * scale);
+        }
+        __syncthreads();
+    }
 }
 
 // ----------------------------------------------------------------------------
 // 1-D: the whole convolution in one CTA. Forward: C0 = w0 + i d_1 and
-// CK' = (K1 + G_1) + i K2, whose spectrum is K1^ + i (S_1 + K2^); K2^ is the
-// even and S_1 the odd part of the imaginary part in k. Products as in 2-D;
-// inverse: D0 = H1 + i U1 -> (h1, u'_1), D1 = V -> v. Node values
-// (h1, u'_1, 0, v) / L; Z = w0 . h1 - N in FP64.
+// CK' = (K1 + lam G_1) + i K2 with lam = 2^-ceil(log2 n) (exact) keeping the odd
+// kernel no larger than the even ones, so its round-off does not swamp K1^.
+// Spectrum of CK': K1^ + i (lam S_1 + K2^); K2^ is the even and lam S_1 the
+// odd part of the imaginary part in k. Z from the Parseval sum; inverse:
+// D0 = U1 + i V -> (u'_1, v). Node values (0, u'_1, 0, v) / L.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
 conv1d_kernel(const long long* __restrict__ w, Params* params, const FftEntry* __restrict__ table,
@@ -424,6 +430,9 @@ conv1d_kernel(const long long* __restrict__ w, Params* params, const FftEntry* _
     const int n = P.n, L = P.L;
     const float2* tw = tw_all + e.tw_off;
     const float inv = P.fx_inv;
+    int lg = 0;
+    while ((1 << lg) < n) ++lg;
+    const float lam = ldexpf(1.0f, -lg), inv_lam = ldexpf(1.0f, lg);
     float2* X = sm;
     float2* Yb = sm + 2 * L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
@@ -433,13 +442,14 @@ conv1d_kernel(const long long* __restrict__ w, Params* params, const FftEntry* _
         if (o >= 0) {
             const float2 k = kernel_pair(P.delta2, o * o);
             const int so = (i < n) ? i : i - L;  // signed offset
-            kv = make_float2(k.x + (float)so * k.y, k.y);
+            kv = make_float2(k.x + lam * (float)so * k.y, k.y);
         }
         X[L + i] = kv;
     }
     __syncthreads();
     float2* F = fft_batch(X, Yb, e, 2, tw, -1.0f);
     float2* O = (F == X) ? Yb : X;
+    double zp = 0.0;
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
         const int kn = (L - k) % L;
         const float2 x = F[k], xm = conjf2(F[kn]);
@@ -447,27 +457,18 @@ conv1d_kernel(const long long* __restrict__ w, Params* params, const FftEntry* _
         const float2 t = csub(x, xm);
         const float2 d1 = make_float2(0.5f * t.y, -0.5f * t.x);
         const float2 ck = F[L + k], ckn = F[L + kn];
-        const float K1 = ck.x, K2 = 0.5f * (ck.y + ckn.y), S1 = 0.5f * (ck.y - ckn.y);
+        const float K1 = ck.x, K2 = 0.5f * (ck.y + ckn.y), S1 = 0.5f * (ck.y - ckn.y) * inv_lam;
+        zp += ((double)w0.x * w0.x + (double)w0.y * w0.y) * (double)K1;
         const float2 u1 = csub(cscale(d1, K2), mul_si(w0, S1));
-        O[k] = cadd(cscale(w0, K1), mul_si(u1, 1.0f));
-        O[L + k] = cscale(w0, K2);
+        O[k] = cadd(u1, mul_si(cscale(w0, K2), 1.0f));
     }
+    const double zt = block_sum_d(zp, sred);
+    if (threadIdx.x == 0) publish_Z(zt / (double)L, params, Z_out, N);
     __syncthreads();
-    const float2* R = fft_batch(O, F, e, 2, tw, 1.0f);
+    const float2* R = fft_batch(O, F, e, 1, tw, 1.0f);
     const float scale = 1.0f / (float)L;
-    double zp = 0.0;
-    for (int g = threadIdx.x; g < n; g += blockDim.x) {
-        const float4 h = make_float4(R[g].x * scale, R[g].y * scale, 0.0f, R[L + g].x * scale);
-        hgrid[g] = h;
-        zp += (double)w[g] * (double)h.x;
-    }
-    const double t = block_sum_d(zp, sred);
-    if (threadIdx.x == 0) {
-        const double Z = t * (double)P.fx_inv - (double)N;
-        params->Z = Z;
-        params->inv_Z = (float)(1.0 / Z);
-        if (Z_out) *Z_out = Z;
-    }
+    for (int g = threadIdx.x; g < n; g += blockDim.x)
+        hgrid[g] = make_float4(0.0f, R[g].x * scale, 0.0f, R[g].y * scale);
 }
 
 // ----------------------------------------------------------------------------
@@ -504,11 +505,11 @@ cudaError_t launch_convolution(tsne_plan* pl, double* Z_out) {
                                                                      pl->twiddles, pl->spec);
         const int g2 = (int)std::min<int64_t>(pl->L_max / 2 + 1, 2 * pl->sm_count);
         cols_kernel<<<g2, 512, smem_cols(pl), pl->stream>>>(pl->params, pl->fft_table, pl->twiddles,
-                                                            pl->spec);
+                                                            pl->spec, pl->z_partial,
+                                                            pl->tickets + 2, Z_out, pl->N);
         const int g3 = (int)std::min<int64_t>(pl->n_max, 4 * pl->sm_count);
         rows_inv_kernel<<<g3, 256, smem_rows_inv(pl), pl->stream>>>(
-            pl->w, pl->params, pl->fft_table, pl->twiddles, pl->spec, pl->hgrid, pl->z_partial,
-            pl->tickets + 2, Z_out, pl->N);
+            pl->params, pl->fft_table, pl->twiddles, pl->spec, pl->hgrid);
         pl->launches += 3;
     } else {
         conv1d_kernel<<<1, 1024, smem_1d(pl), pl->stream>>>(pl->w, pl->params, pl->fft_table,

@@ -93,7 +93,7 @@ struct tsne_plan {
     long long* w;            // [(s+1) * n_max^s] spread grids, fixed point 2^-fx_shift
     float2* spec;            // [4 * n_max * L_max] row spectra (s = 2)
     float4* hgrid;           // [n_max^s] node potentials
-    double* z_partial;       // [n_max]
+    double* z_partial;       // [L_max / 2 + 1] Parseval sums of Z per column pair
     double* kl_partial;      // [kl_blocks]
     double* kl_out_dev;      // [1]
     int32_t* valid_flag;     // [1]

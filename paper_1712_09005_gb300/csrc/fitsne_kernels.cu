@@ -538,132 +538,167 @@ __device__ __forceinline__ void attract(float yi0, float yi1, int j, float v,
     if (S == 2) {
         const float2 yj = __ldg(reinterpret_cast<const float2*>(Y) + j);
         const float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
-        const float q = v * __frcp_rn(1.0f + d0 * d0 + d1 * d1);
+        const float q = __fdividef(v, 1.0f + d0 * d0 + d1 * d1);
         a0 += q * d0;
         a1 += q * d1;
     } else {
         const float d0 = yi0 - __ldg(Y + j);
-        a0 += v * __frcp_rn(1.0f + d0 * d0) * d0;
+        a0 += __fdividef(v, 1.0f + d0 * d0) * d0;
     }
 }
 
-// Software-pipelined: while row i is finished, the column indices and values
-// of the warp's next row (up to 32 U entries) are already in flight, and the
-// per-row loads of row i (its coordinates, its box's node values, the
-// optimizer state) are issued before the attraction loop waits on gathers.
-template <int S, int PP, bool STEP>
-__global__ void __launch_bounds__(256)
-force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-             const float* __restrict__ val, const float* __restrict__ Y,
-             const Params* __restrict__ params, const float4* __restrict__ hgrid, float alpha,
-             float* __restrict__ dY, StepArgs sa, int64_t N) {
-    constexpr int NODES = (S == 2) ? PP * PP : PP;
-    constexpr int U = 8;
-    const Params P = *params;
-    if (P.error) return;
-    const int lane = threadIdx.x % 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
-    const float fs = P.delta * P.inv_Z;
-    const int n = P.n;
-    // this lane's node of the p^s nodes of a box
-    const int j1 = (S == 2) ? lane / PP : lane;
-    const int j2 = (S == 2) ? lane % PP : 0;
-    const bool node_lane = lane < NODES;
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    if (i >= N) return;
-    int beg = __ldg(&row_ptr[i]), end = __ldg(&row_ptr[i + 1]);
-    int jj[U];
-    float vv[U];
+template <int U>
+__device__ __forceinline__ void load_slots(const int32_t* __restrict__ col,
+                                           const float* __restrict__ val, int beg, int end,
+                                           int lane, int (&jj)[U], float (&vv)[U]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int e = beg + lane + 32 * u;
         jj[u] = e < end ? __ldcs(&col[e]) : 0;
         vv[u] = e < end ? __ldcs(&val[e]) : 0.0f;
     }
-    while (true) {
-        const int64_t inext = i + nwarp;
-        int nbeg = 0, nend = 0;
-        if (inext < N) {
-            nbeg = __ldg(&row_ptr[inext]);
-            nend = __ldg(&row_ptr[inext + 1]);
-        }
-        float yi0, yi1 = 0.0f;
-        if (S == 2) {
-            const float2 t = reinterpret_cast<const float2*>(Y)[i];
-            yi0 = t.x;
-            yi1 = t.y;
-        } else {
-            yi0 = Y[i];
-        }
-        float2 us = make_float2(0.0f, 0.0f), gs = make_float2(0.0f, 0.0f);
-        if (STEP && lane == 0) {
-            if (S == 2) {
-                us = reinterpret_cast<const float2*>(sa.uY)[i];
-                gs = reinterpret_cast<const float2*>(sa.gains)[i];
-            } else {
-                us.x = sa.uY[i];
-                gs.x = sa.gains[i];
-            }
-        }
-        // Step 3 weights of this lane's node, and its node values (loaded early)
-        float wt = 0.0f, o1 = 0.0f, o2 = 0.0f;
-        float4 h = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (node_lane) {
-            const int l1 = interval_of(yi0, P);
-            float L1[PP];
-            const float t1 = local_t(yi0, l1, P);
-            lagrange<PP>(t1, L1);
-            float w1 = 0.0f;
+}
+
+// Attraction of one row from its prefetched entries (and any beyond 32 U),
+// summed over the warp.
+template <int S, int U>
+__device__ __forceinline__ void attract_row(const int32_t* __restrict__ col,
+                                            const float* __restrict__ val,
+                                            const float* __restrict__ Y, int beg, int end,
+                                            float yi0, float yi1, int lane, const int (&jj)[U],
+                                            const float (&vv)[U], float& a0, float& a1) {
+    a0 = 0.0f;
+    a1 = 0.0f;
 #pragma unroll
-            for (int k = 0; k < PP; ++k) if (k == j1) w1 = L1[k];
-            wt = w1;
-            o1 = ((float)j1 + 0.5f) - t1;
-            int64_t gi;
+    for (int u = 0; u < U; ++u)
+        if (beg + lane + 32 * u < end) attract<S>(yi0, yi1, jj[u], vv[u], Y, a0, a1);
+    for (int e = beg + lane + 32 * U; e < end; e += 32)
+        attract<S>(yi0, yi1, __ldcs(&col[e]), __ldcs(&val[e]), Y, a0, a1);
+    a0 = warp_sum(a0);
+    if (S == 2) a1 = warp_sum(a1);
+}
+
+// Each warp owns blocks of 32 consecutive points (rows of P). Per block:
+//  1. lane l takes point i0 + l: its row bounds, coordinates, optimizer state
+//     (coalesced), its box, local coordinates and Lagrange weights, and the
+//     Step 3 interpolation of the node values of its box -> F_rep;
+//  2. the warp walks the 32 rows of P; each row's entries are spread over
+//     the lanes, and row r + 1's entries are loaded before row r's are used;
+//     the row sum lands in lane r;
+//  3. lane l forms dY (or the update) of its point; stores are coalesced.
+#ifndef FITSNE_FORCE_SLOTS
+#define FITSNE_FORCE_SLOTS 6  // prefetched entries per lane per row
+#endif
+#ifndef FITSNE_FORCE_MINB
+#define FITSNE_FORCE_MINB 3   // resident 256-thread blocks per SM the registers must allow
+#endif
+
+template <int S, int PP, bool STEP>
+__global__ void __launch_bounds__(256, FITSNE_FORCE_MINB)
+force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+             const float* __restrict__ val, const float* __restrict__ Y,
+             const Params* __restrict__ params, const float4* __restrict__ hgrid, float alpha,
+             float* __restrict__ dY, StepArgs sa, int64_t N) {
+    constexpr int U = FITSNE_FORCE_SLOTS;
+    const Params P = *params;
+    if (P.error) return;
+    const int lane = threadIdx.x % 32;
+    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
+    const float fs = P.delta * P.inv_Z;
+    const int n = P.n;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32 * 32; i0 < N;
+         i0 += nwarp * 32) {
+        const int64_t i = i0 + lane;
+        const bool live = i < N;
+        const int nrows = (N - i0) < 32 ? (int)(N - i0) : 32;
+        // 1. per-point work, one point per lane
+        int rp_lo = 0, rp_hi = 0;
+        float yi0 = 0.0f, yi1 = 0.0f, f0 = 0.0f, f1 = 0.0f;
+        float2 us = make_float2(0.0f, 0.0f), gs = make_float2(0.0f, 0.0f);
+        if (live) {
+            rp_lo = __ldg(&row_ptr[i]);
+            rp_hi = __ldg(&row_ptr[i + 1]);
+            if (S == 2) {
+                const float2 t = reinterpret_cast<const float2*>(Y)[i];
+                yi0 = t.x;
+                yi1 = t.y;
+            } else {
+                yi0 = Y[i];
+            }
+            if (STEP) {
+                if (S == 2) {
+                    us = reinterpret_cast<const float2*>(sa.uY)[i];
+                    gs = reinterpret_cast<const float2*>(sa.gains)[i];
+                } else {
+                    us.x = sa.uY[i];
+                    gs.x = sa.gains[i];
+                }
+            }
+            // Step 3: (h_{m+1} - y(m) h_{s+2})(y_i) = delta sum_g L_g [u'_m + (j_m + 1/2 - t_m) v]
+            const int l1 = interval_of(yi0, P);
+            const float t1 = local_t(yi0, l1, P);
+            float L1[PP];
+            lagrange<PP>(t1, L1);
             if (S == 2) {
                 const int l2 = interval_of(yi1, P);
-                float L2[PP];
                 const float t2 = local_t(yi1, l2, P);
+                float L2[PP];
                 lagrange<PP>(t2, L2);
-                float w2 = 0.0f;
 #pragma unroll
-                for (int k = 0; k < PP; ++k) if (k == j2) w2 = L2[k];
-                wt = w1 * w2;
-                o2 = ((float)j2 + 0.5f) - t2;
-                gi = (int64_t)(l1 * PP + j1) * n + (l2 * PP + j2);
+                for (int j1 = 0; j1 < PP; ++j1) {
+                    const float4* row = hgrid + (int64_t)(l1 * PP + j1) * n + l2 * PP;
+                    const float o1 = ((float)j1 + 0.5f) - t1;
+#pragma unroll
+                    for (int j2 = 0; j2 < PP; ++j2) {
+                        const float4 h = __ldg(row + j2);  // (h1, u'1, u'2, v)
+                        const float wt = L1[j1] * L2[j2];
+                        const float o2 = ((float)j2 + 0.5f) - t2;
+                        f0 += wt * __fmaf_rn(o1, h.w, h.y);
+                        f1 += wt * __fmaf_rn(o2, h.w, h.z);
+                    }
+                }
             } else {
-                gi = l1 * PP + j1;
-            }
-            h = __ldg(&hgrid[gi]);  // (h1, u'1, u'2, v_{s+2})
-        }
-        // attraction over the prefetched entries, then any beyond 32 U
-        float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (beg + lane + 32 * u < end) attract<S>(yi0, yi1, jj[u], vv[u], Y, a0, a1);
-        for (int e = beg + lane + 32 * U; e < end; e += 32)
-            attract<S>(yi0, yi1, __ldcs(&col[e]), __ldcs(&val[e]), Y, a0, a1);
-        // prefetch the next row
-        if (inext < N) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = nbeg + lane + 32 * u;
-                jj[u] = e < nend ? __ldcs(&col[e]) : 0;
-                vv[u] = e < nend ? __ldcs(&val[e]) : 0.0f;
+                for (int j1 = 0; j1 < PP; ++j1) {
+                    const float4 h = __ldg(hgrid + l1 * PP + j1);
+                    f0 += L1[j1] * __fmaf_rn(((float)j1 + 0.5f) - t1, h.w, h.y);
+                }
             }
         }
-        a0 = warp_sum(a0);
-        if (S == 2) a1 = warp_sum(a1);
-        float r1 = wt * __fmaf_rn(o1, h.w, h.y);
-        float r2 = (S == 2) ? wt * __fmaf_rn(o2, h.w, h.z) : 0.0f;
-#pragma unroll
-        for (int o = (NODES > 16 ? 16 : (NODES > 8 ? 8 : (NODES > 4 ? 4 : (NODES > 2 ? 2 : 1))));
-             o >= 1; o >>= 1) {
-            r1 += __shfl_xor_sync(kFull, r1, o);
-            if (S == 2) r2 += __shfl_xor_sync(kFull, r2, o);
+        // 2. attraction, row by row, next row's entries in flight
+        float A0 = 0.0f, A1 = 0.0f;
+        int jA[U], jB[U];
+        float vA[U], vB[U];
+        {
+            const int b0 = __shfl_sync(kFull, rp_lo, 0), e0 = __shfl_sync(kFull, rp_hi, 0);
+            load_slots<U>(col, val, b0, e0, lane, jA, vA);
         }
-        if (lane == 0) {
-            const float g0 = 4.0f * (alpha * a0 + r1 * fs);
-            const float g1 = (S == 2) ? 4.0f * (alpha * a1 + r2 * fs) : 0.0f;
+        for (int r = 0; r < nrows; r += 2) {
+            const int bA = __shfl_sync(kFull, rp_lo, r), eA = __shfl_sync(kFull, rp_hi, r);
+            const int bB = __shfl_sync(kFull, rp_lo, r + 1), eB = __shfl_sync(kFull, rp_hi, r + 1);
+            const bool hasB = r + 1 < nrows;
+            if (hasB) load_slots<U>(col, val, bB, eB, lane, jB, vB);
+            {
+                const float y0 = __shfl_sync(kFull, yi0, r), y1 = __shfl_sync(kFull, yi1, r);
+                float a0, a1;
+                attract_row<S, U>(col, val, Y, bA, eA, y0, y1, lane, jA, vA, a0, a1);
+                if (lane == r) { A0 = a0; A1 = a1; }
+            }
+            if (hasB) {
+                if (r + 2 < nrows) {
+                    const int bC = __shfl_sync(kFull, rp_lo, r + 2), eC = __shfl_sync(kFull, rp_hi, r + 2);
+                    load_slots<U>(col, val, bC, eC, lane, jA, vA);
+                }
+                const float y0 = __shfl_sync(kFull, yi0, r + 1), y1 = __shfl_sync(kFull, yi1, r + 1);
+                float a0, a1;
+                attract_row<S, U>(col, val, Y, bB, eB, y0, y1, lane, jB, vB, a0, a1);
+                if (lane == r + 1) { A0 = a0; A1 = a1; }
+            }
+        }
+        // 3. gradient (and update) of this lane's point
+        if (live) {
+            const float g0 = 4.0f * (alpha * A0 + f0 * fs);
+            const float g1 = (S == 2) ? 4.0f * (alpha * A1 + f1 * fs) : 0.0f;
             if (!STEP) {
                 if (S == 2) reinterpret_cast<float2*>(dY)[i] = make_float2(g0, g1);
                 else dY[i] = g0;
@@ -681,10 +716,6 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
                 }
             }
         }
-        if (inext >= N) break;
-        i = inext;
-        beg = nbeg;
-        end = nend;
     }
 }
 
@@ -836,7 +867,7 @@ cudaError_t launch_sort_and_spread(tsne_plan* pl, const float* Y) {
 template <int S, int PP, bool STEP>
 static void force_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha, float* dY,
                        StepArgs sa) {
-    const int g = grid_for(pl, pl->N * 32, 256, 8);
+    const int g = grid_for(pl, pl->N, 256, 8);
     force_kernel<S, PP, STEP><<<g, 256, 0, pl->stream>>>(P.row_ptr, P.col, P.val, Y, pl->params,
                                                          pl->hgrid, alpha, dY, sa, pl->N);
     pl->launches += 1;

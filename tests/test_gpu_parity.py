@@ -114,7 +114,8 @@ def test_spread_grids(s):
 @pytest.mark.parametrize("s", [1, 2])
 def test_fft_convolution_against_cufft(s):
     """Step 2: the hand-written FFT convolution equals cuFFT (torch.fft, FP64) applied
-    to the same spread grids: (h1, u'_1, u'_2, v) = (K1*w0, K2*d1 - G1*w0, K2*d2 - G2*w0, K2*w0)."""
+    to the same spread grids: (u'_1, u'_2, v) = (K2*d1 - G1*w0, K2*d2 - G2*w0, K2*w0), and
+    Z + N = w0 . (K1 * w0)."""
     N = 3000
     P = affinities(N, 3)
     Y = clustered_Y(N, s, 40.0, seed=11)
@@ -139,7 +140,8 @@ def test_fft_convolution_against_cufft(s):
         F = torch.fft.fft(pad)
         conv = lambda a, K: torch.fft.ifft(F[a] * torch.fft.fft(K)).real[:n]
         zero = torch.zeros(n, dtype=f64, device=dev)
-        want = torch.stack([conv(0, K1), conv(1, K2) - conv(0, G1), zero, conv(0, K2)], dim=1)
+        want_h1 = conv(0, K1)
+        want = torch.stack([want_h1, conv(1, K2) - conv(0, G1), zero, conv(0, K2)], dim=1)
     else:
         O1, O2 = off[:, None].expand(L, L), off[None, :].expand(L, L)
         K1 = 1 / (1 + (O1 * delta) ** 2 + (O2 * delta) ** 2)
@@ -148,12 +150,15 @@ def test_fft_convolution_against_cufft(s):
         pad[:, :n, :n] = torch.as_tensor(w.reshape(3, n, n), device=dev)
         F = torch.fft.fft2(pad)
         conv = lambda a, K: torch.fft.ifft2(F[a] * torch.fft.fft2(K)).real[:n, :n].reshape(-1)
-        want = torch.stack([conv(0, K1), conv(1, K2) - conv(0, O1 * K2),
+        want_h1 = conv(0, K1)
+        want = torch.stack([want_h1, conv(1, K2) - conv(0, O1 * K2),
                             conv(2, K2) - conv(0, O2 * K2), conv(0, K2)], dim=1)
     want = want.cpu().numpy()
-    for k in ([0, 1, 3] if s == 1 else [0, 1, 2, 3]):
+    for k in ([1, 3] if s == 1 else [1, 2, 3]):
         scale = np.abs(want[:, k]).max()
         assert np.abs(h[:, k] - want[:, k]).max() <= 5e-6 * scale, k
+    zn = float((torch.as_tensor(w.reshape(s + 1, -1)[0], device=dev) * want_h1).sum())
+    assert abs(info["Z"] + N - zn) <= 5e-7 * zn
 
 
 @pytest.mark.parametrize("s", [1, 2])
