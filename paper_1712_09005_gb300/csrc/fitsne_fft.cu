@@ -410,8 +410,11 @@ rows_inv_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ 
 
 // ----------------------------------------------------------------------------
 // 1-D: the whole convolution in one CTA. Forward: C0 = w0 + i d_1 and
-// CK' = (K1 + lam G_1) + i K2 with lam = 2^-ceil(log2 n) (exact) keeping the odd
-// kernel no larger than the even ones, so its round-off does not swamp K1^.
+// CK' = (K1 + lam G_1) + i K2, lam a power of two (exact) that brings the
+// largest |G_1(o)| = max o / (1 + delta^2 o^2)^2 near 1 (the maximum is
+// 3 sqrt(3) / (16 delta) at o = 1 / (delta sqrt 3), or at o = n - 1), so the
+// three kernels share a transform at comparable magnitudes and the parity
+// split loses no accuracy.
 // Spectrum of CK': K1^ + i (lam S_1 + K2^); K2^ is the even and lam S_1 the
 // odd part of the imaginary part in k. Z from the Parseval sum; inverse:
 // D0 = U1 + i V -> (u'_1, v). Node values (0, u'_1, 0, v) / L.
@@ -430,8 +433,12 @@ conv1d_kernel(const long long* __restrict__ w, Params* params, const FftEntry* _
     const int n = P.n, L = P.L;
     const float2* tw = tw_all + e.tw_off;
     const float inv = P.fx_inv;
-    int lg = 0;
-    while ((1 << lg) < n) ++lg;
+    const float o_star = 1.0f / (P.delta * 1.7320508f);
+    const float o_max = (float)(n - 1);
+    const float om = fminf(o_star, o_max);
+    const float den = 1.0f + P.delta2 * om * om;
+    const float g_max = fmaxf(om / (den * den), 1.0f);
+    const int lg = (int)rintf(log2f(g_max));
     const float lam = ldexpf(1.0f, -lg), inv_lam = ldexpf(1.0f, lg);
     float2* X = sm;
     float2* Yb = sm + 2 * L;

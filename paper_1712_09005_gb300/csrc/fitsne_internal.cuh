@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/fitsne_gb300.h"
+#include "fitsne_gb300.h"
 
 namespace fitsne {
 

@@ -226,7 +226,8 @@ def test_two_points_and_degenerate_box():
             dY, Z = plan.gradient(pkg.DeviceCSR.from_host(*P), torch.as_tensor(Y, device="cuda"), 3.0)
             torch.cuda.synchronize()
         ref = oracle.interp_gradient(Y.astype(np.float64), P, alpha=3.0, opts=oracle_opts(2))
-        np.testing.assert_allclose(dY.cpu().numpy(), ref["dY"], rtol=1e-5, atol=1e-6)
+        # coincident points: the exact forces vanish; FP32 leaves O(1e-6) residue
+        np.testing.assert_allclose(dY.cpu().numpy(), ref["dY"], rtol=1e-5, atol=1e-5)
         # with N = 2, Z (about 0.67) is the small difference sum h1 - N of two
         # O(1) terms, so its error is bounded relative to sum h1 = Z + N
         assert abs(Z.item() - ref["Z"]) <= Z_TOL * (abs(ref["Z"]) + 2)
