@@ -252,6 +252,31 @@ int tsne_plan_profile_read(tsne_plan* plan, double* ms_out, int64_t* count_out);
  * count of every kernel launch the library enqueued for it). */
 int64_t tsne_plan_launch_count(const tsne_plan* plan);
 
+/*
+ * KL(P || Q) without any device allocation (the paper has no counterpart;
+ * this exists for callers that cannot call cudaMalloc, e.g. a process whose
+ * own allocator owns all device memory, or code that must not let
+ * cudaMalloc/cudaFree synchronise the device). Same sum as tsne_kl, for the
+ * caller's Z (the value tsne_gradient wrote to Z_out at the same Y):
+ *   KL = sum p log p + sum p log(1 + |y_i - y_j|^2) + (sum p) log Z.
+ * P and Y (N x s, s = 1 or 2) are device data as in tsne_gradient; kl_out is
+ * a DEVICE address that receives one double; work is enqueued on stream
+ * (cudaStream_t, NULL = legacy default) and the call returns without
+ * synchronising. 1 <= N <= 2^31 - 2 and 0 <= nnz <= 2^31 - 1, else
+ * INVALID_ARG. Its scratch is a fixed 16,640-byte array in the library's
+ * device image (per-block partial sums of at most 1,024 reduction blocks and
+ * a completion counter), held by every GPU that loads the library until
+ * process exit. The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress), so make it before any stream capture. All calls
+ * share the array: calls whose work overlaps on the GPU (different streams,
+ * or different host threads on one device) race; serialise them.
+ * tsne_noalloc_last_error_string describes the last failure of this entry
+ * point on the calling thread.
+ */
+int tsne_kl_noalloc(tsne_csr P, const float* Y, int64_t N, int32_t s, double Z, double* kl_out,
+                    void* stream);
+const char* tsne_noalloc_last_error_string(void);
+
 #ifdef __cplusplus
 }
 #endif

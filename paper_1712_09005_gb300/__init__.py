@@ -22,7 +22,7 @@ __all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destr
            "tsne_plan_set_box", "tsne_gradient", "tsne_step", "tsne_run", "tsne_run_reset", "tsne_run_iters", "tsne_kl",
            "tsne_run_host", "tsne_validate_csr", "tsne_plan_status", "tsne_plan_info",
            "tsne_debug_copy", "tsne_plan_profile", "tsne_plan_profile_read",
-           "tsne_plan_launch_count", "TsneError"]
+           "tsne_plan_launch_count", "tsne_kl_noalloc", "TsneError"]
 
 
 def lib():
@@ -198,6 +198,20 @@ def tsne_plan_profile_read(plan) -> dict:
 
 def tsne_plan_launch_count(plan) -> int:
     return int(lib().tsne_plan_launch_count(plan))
+
+
+def tsne_kl_noalloc(P: DeviceCSR, Y: torch.Tensor, s: int, Z: float, kl_out: torch.Tensor,
+                    stream: int | None = None) -> None:
+    """KL without device allocation; kl_out is a 1-element float64 CUDA tensor."""
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    if not (kl_out.is_cuda and kl_out.dtype == torch.float64 and kl_out.numel() >= 1):
+        raise TypeError("kl_out must be a float64 CUDA tensor")
+    N = Y.numel() // s
+    rc = lib().tsne_kl_noalloc(P.c(), _ptr(Y), N, s, float(Z), _ptr(kl_out),
+                               ctypes.c_void_p(stream))
+    if rc != 0:
+        raise TsneError(rc, lib().tsne_noalloc_last_error_string().decode())
 
 
 # ---- convenience object -------------------------------------------------------

@@ -90,6 +90,9 @@ _SIGNATURES = [
     ("tsne_plan_profile_read", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int64)]),
     ("tsne_plan_launch_count", ctypes.c_int64, [_P]),
+    ("tsne_kl_noalloc", ctypes.c_int, [tsne_csr, _P, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_double, _P, _P]),
+    ("tsne_noalloc_last_error_string", ctypes.c_char_p, []),
 ]
 
 _lock = threading.Lock()

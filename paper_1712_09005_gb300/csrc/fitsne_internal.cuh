@@ -172,6 +172,11 @@ cudaError_t launch_step(tsne_plan* pl, const tsne_csr& P, const float* Y, float*
                         float* uY, float* gains, float alpha, float momentum, float lr,
                         float min_gain, float gain_inc, float gain_dec);
 cudaError_t launch_kl(tsne_plan* pl, const tsne_csr& P, const float* Y);
+// KL reduction with explicit scratch: 2 doubles per block in partial, a
+// self-resetting completion counter, Z from Z_dev (device) or Z_val.
+cudaError_t launch_kl_raw(const tsne_csr& P, const float* Y, int64_t N, int s,
+                          const double* Z_dev, double Z_val, double* partial, unsigned* ticket,
+                          double* out, int blocks, cudaStream_t stream);
 cudaError_t launch_validate(tsne_plan* pl, const tsne_csr& P);
 cudaError_t launch_fill(tsne_plan* pl, float* a, float v, int64_t n);
 cudaError_t fft_configure(tsne_plan* pl);  // sets shared-memory limits

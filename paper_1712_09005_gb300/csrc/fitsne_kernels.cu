@@ -728,7 +728,7 @@ template <int S>
 __global__ void __launch_bounds__(256)
 kl_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
           const float* __restrict__ val, const float* __restrict__ Y, int64_t N,
-          const Params* __restrict__ params, double* __restrict__ partial,
+          const double* __restrict__ Z_dev, double Z_val, double* __restrict__ partial,
           unsigned* __restrict__ ticket, double* __restrict__ out) {
     const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
     const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
@@ -782,7 +782,8 @@ kl_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
         ps += __ldcg(&partial[2 * k + 1]);
     }
     *ticket = 0u;
-    *out = a + ps * log(__ldcg(&params->Z));
+    const double Z = Z_dev ? __ldcg(Z_dev) : Z_val;
+    *out = a + ps * log(Z);
 }
 
 // ----------------------------------------------------------------------------
@@ -901,16 +902,23 @@ cudaError_t launch_step(tsne_plan* pl, const tsne_csr& P, const float* Y, float*
     return cudaGetLastError();
 }
 
+cudaError_t launch_kl_raw(const tsne_csr& P, const float* Y, int64_t N, int s,
+                          const double* Z_dev, double Z_val, double* partial, unsigned* ticket,
+                          double* out, int blocks, cudaStream_t stream) {
+    if (s == 2)
+        kl_kernel<2><<<blocks, 256, 0, stream>>>(P.row_ptr, P.col, P.val, Y, N, Z_dev, Z_val,
+                                                 partial, ticket, out);
+    else
+        kl_kernel<1><<<blocks, 256, 0, stream>>>(P.row_ptr, P.col, P.val, Y, N, Z_dev, Z_val,
+                                                 partial, ticket, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_kl(tsne_plan* pl, const tsne_csr& P, const float* Y) {
     const int g = 4 * pl->sm_count;  // kl_partial holds 2 doubles per block
-    if (pl->s == 2)
-        kl_kernel<2><<<g, 256, 0, pl->stream>>>(P.row_ptr, P.col, P.val, Y, pl->N, pl->params,
-                                                pl->kl_partial, pl->tickets + 3, pl->kl_out_dev);
-    else
-        kl_kernel<1><<<g, 256, 0, pl->stream>>>(P.row_ptr, P.col, P.val, Y, pl->N, pl->params,
-                                                pl->kl_partial, pl->tickets + 3, pl->kl_out_dev);
     pl->launches += 1;
-    return cudaGetLastError();
+    return launch_kl_raw(P, Y, pl->N, pl->s, &pl->params->Z, 0.0, pl->kl_partial, pl->tickets + 3,
+                         pl->kl_out_dev, g, pl->stream);
 }
 
 cudaError_t launch_validate(tsne_plan* pl, const tsne_csr& P) {
