@@ -372,6 +372,7 @@ scan_boxes_kernel(int32_t* __restrict__ counts, const Params* __restrict__ param
     __shared__ int sw[32];
     const Params P = *params;
     const int nb = P.n_boxes;
+    if (blockIdx.x * kScanBlock >= nb) return;  // uniform per block
     const int base = blockIdx.x * kScanBlock + threadIdx.x * 2;
     int c[2] = {base < nb ? counts[base] : 0, base + 1 < nb ? counts[base + 1] : 0};
     int k[2] = {(c[0] + kChunk - 1) / kChunk, (c[1] + kChunk - 1) / kChunk};
@@ -590,7 +591,7 @@ __device__ __forceinline__ void attract_row(const int32_t* __restrict__ col,
 #define FITSNE_FORCE_SLOTS 6  // prefetched entries per lane per row
 #endif
 #ifndef FITSNE_FORCE_MINB
-#define FITSNE_FORCE_MINB 3   // resident 256-thread blocks per SM the registers must allow
+#define FITSNE_FORCE_MINB 4   // resident 256-thread blocks per SM the registers must allow
 #endif
 
 template <int S, int PP, bool STEP>
