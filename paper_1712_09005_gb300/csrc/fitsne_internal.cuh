@@ -11,13 +11,13 @@
 namespace fitsne {
 
 constexpr int kWarp = 32;
-constexpr int kChunk = 256;       // sorted points per spread work item
+constexpr int kChunk = 128;       // sorted points per spread work item
 constexpr int kMaxStages = 16;    // radix stages of one FFT
 constexpr int kScanBlock = 2048;  // boxes per scan block (1024 threads x 2)
 constexpr int kBoxThreads = 256;  // threads of the bounding-box blocks
 constexpr int kBoxBlocks = 304;   // 2 per SM on 152 SMs
 constexpr int kHistBins = 12288;  // boxes that fit a shared-memory histogram (48 KB)
-constexpr int kSortPts = 8192;    // points per block of the shared-memory sort kernels
+constexpr int kSortPts = 2048;    // points per block of the sort kernels (256 threads x 8)
 
 // One FFT length of the plan's table: L = product of radix[0..nst), each
 // radix in {2, 3, 4, 5}; tw_off locates its L twiddles exp(-2 pi i j / L).

@@ -203,13 +203,19 @@ box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_f
 // (tight clusters) from serialising on one global atomic; with more boxes
 // (each then holds few points) it uses the global counters directly.
 template <int S>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 count_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ params,
-             int32_t* __restrict__ counts) {
+             int32_t* __restrict__ counts, long long* __restrict__ w) {
     extern __shared__ int32_t hist[];
     const Params P = *params;
     if (P.error) return;
     const int nb = P.n_boxes;
+    {  // the spread grids of this iteration start at zero
+        const int64_t G = (S == 2) ? (int64_t)P.n * P.n : P.n;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < (S + 1) * G; g += stride)
+            w[g] = 0;
+    }
     const bool local = nb <= kHistBins;
     const int lane = threadIdx.x % 32;
     if (local) {
@@ -217,8 +223,8 @@ count_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ 
         __syncthreads();
     }
     const int64_t p0 = (int64_t)blockIdx.x * kSortPts;
-    for (int k = 0; k < kSortPts / 1024; ++k) {
-        const int64_t i = p0 + k * 1024 + threadIdx.x;
+    for (int k = 0; k < kSortPts / 256; ++k) {
+        const int64_t i = p0 + k * 256 + threadIdx.x;
         const int box = (i < N) ? box_of<S>(Y, i, P) : -1;
         const unsigned peers = __match_any_sync(kFull, box);
         if (box >= 0 && lane == __ffs(peers) - 1) {
@@ -237,11 +243,11 @@ count_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ 
 // per box in the global cursors, then places each point at its box's range
 // plus its rank inside the block.
 template <int S>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 scatter_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ params,
                int32_t* __restrict__ cursor, float* __restrict__ sorted_y) {
     extern __shared__ int32_t hist[];
-    constexpr int K = kSortPts / 1024;
+    constexpr int K = kSortPts / 256;
     const Params P = *params;
     if (P.error) return;
     const int nb = P.n_boxes;
@@ -252,7 +258,7 @@ scatter_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict_
     int box[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int64_t i = p0 + k * 1024 + threadIdx.x;
+        const int64_t i = p0 + k * 256 + threadIdx.x;
         box[k] = (i < N) ? box_of<S>(Y, i, P) : -1;
     }
     if (local) {
@@ -277,7 +283,7 @@ scatter_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict_
         if (box[k] >= 0 && lane == leader) pos = atomicAdd(&dst_cursor[box[k]], __popc(peers));
         pos = __shfl_sync(kFull, pos, leader) + __popc(peers & lt);
         if (box[k] >= 0) {
-            const int64_t i = p0 + k * 1024 + threadIdx.x;
+            const int64_t i = p0 + k * 256 + threadIdx.x;
             if (S == 2)
                 reinterpret_cast<float2*>(sorted_y)[pos] = reinterpret_cast<const float2*>(Y)[i];
             else
@@ -361,44 +367,35 @@ scan_blocks_kernel(const int32_t* __restrict__ counts, Params* params,
 }
 
 // Pass 2: box offsets, scatter cursors, chunk -> box table; resets the counts
-// and zeroes each box's nodes in the spread grids.
+// for the next iteration. Each warp writes the chunk entries of its 64 boxes
+// with its lanes in parallel (a box holding many points has many chunks).
 template <int S, int PP>
 __global__ void __launch_bounds__(1024)
 scan_boxes_kernel(int32_t* __restrict__ counts, const Params* __restrict__ params,
                   const int32_t* __restrict__ block_pts, const int32_t* __restrict__ block_chunks,
                   int32_t* __restrict__ box_start, int32_t* __restrict__ cursor,
-                  int32_t* __restrict__ chunk_start, int32_t* __restrict__ chunk_box,
-                  long long* __restrict__ w, int64_t N) {
+                  int32_t* __restrict__ chunk_start, int32_t* __restrict__ chunk_box, int64_t N) {
     __shared__ int sw[32];
     const Params P = *params;
     const int nb = P.n_boxes;
     if (blockIdx.x * kScanBlock >= nb) return;  // uniform per block
+    const int lane = threadIdx.x % 32;
     const int base = blockIdx.x * kScanBlock + threadIdx.x * 2;
     int c[2] = {base < nb ? counts[base] : 0, base + 1 < nb ? counts[base + 1] : 0};
     int k[2] = {(c[0] + kChunk - 1) / kChunk, (c[1] + kChunk - 1) / kChunk};
     int tp, tc;
     int ep = block_exclusive_scan(c[0] + c[1], sw, tp) + block_pts[blockIdx.x];
     int ec = block_exclusive_scan(k[0] + k[1], sw, tc) + block_chunks[blockIdx.x];
-    const int n = P.n;
-    const int64_t G = (S == 2) ? (int64_t)n * n : n;
+    int ecb[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const int b = base + u;
+        ecb[u] = ec;
         if (b < nb) {
             box_start[b] = ep;
             cursor[b] = ep;
             chunk_start[b] = ec;
             counts[b] = 0;
-            for (int q = 0; q < k[u]; ++q) chunk_box[ec + q] = b;
-            const int bx = (S == 2) ? b / P.n_int : b;
-            const int by = (S == 2) ? b % P.n_int : 0;
-            for (int ch = 0; ch <= S; ++ch)
-                for (int j1 = 0; j1 < PP; ++j1)
-                    for (int j2 = 0; j2 < (S == 2 ? PP : 1); ++j2) {
-                        int64_t g = (S == 2) ? (int64_t)(bx * PP + j1) * n + (by * PP + j2)
-                                             : (int64_t)(bx * PP + j1);
-                        w[ch * G + g] = 0;
-                    }
             if (b == nb - 1) {
                 box_start[nb] = (int32_t)N;
                 chunk_start[nb] = ec + k[u];
@@ -406,6 +403,17 @@ scan_boxes_kernel(int32_t* __restrict__ counts, const Params* __restrict__ param
         }
         ep += c[u];
         ec += k[u];
+    }
+    // chunk -> box entries: the warp visits its lanes' boxes one by one
+    for (int src = 0; src < 32; ++src) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int b = __shfl_sync(kFull, base + u, src);
+            const int kb = __shfl_sync(kFull, k[u], src);
+            const int eb = __shfl_sync(kFull, ecb[u], src);
+            if (b < nb)
+                for (int q = lane; q < kb; q += 32) chunk_box[eb + q] = b;
+        }
     }
 }
 
@@ -533,17 +541,22 @@ __device__ __forceinline__ float update_one(float y, float dy, float& u, float& 
     return y + u;
 }
 
+#ifndef FITSNE_GATHER_L2_ONLY
+#define FITSNE_GATHER_L2_ONLY 0  // 1: the Y[j] gathers bypass L1 (ld.global.cg)
+#endif
+
 template <int S>
 __device__ __forceinline__ void attract(float yi0, float yi1, int j, float v,
                                         const float* __restrict__ Y, float& a0, float& a1) {
     if (S == 2) {
-        const float2 yj = __ldg(reinterpret_cast<const float2*>(Y) + j);
+        const float2 yj = FITSNE_GATHER_L2_ONLY ? __ldcg(reinterpret_cast<const float2*>(Y) + j)
+                                                : __ldg(reinterpret_cast<const float2*>(Y) + j);
         const float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
         const float q = __fdividef(v, 1.0f + d0 * d0 + d1 * d1);
         a0 += q * d0;
         a1 += q * d1;
     } else {
-        const float d0 = yi0 - __ldg(Y + j);
+        const float d0 = yi0 - (FITSNE_GATHER_L2_ONLY ? __ldcg(Y + j) : __ldg(Y + j));
         a0 += __fdividef(v, 1.0f + d0 * d0) * d0;
     }
 }
@@ -839,13 +852,13 @@ template <int S, int PP>
 static void sort_and_spread_impl(tsne_plan* pl, const float* Y) {
     const int gp = (int)((pl->N + kSortPts - 1) / kSortPts);
     const size_t hs = sizeof(int32_t) * kHistBins;
-    count_kernel<S><<<gp, 1024, hs, pl->stream>>>(Y, pl->N, pl->params, pl->counts);
+    count_kernel<S><<<gp, 256, hs, pl->stream>>>(Y, pl->N, pl->params, pl->counts, pl->w);
     scan_blocks_kernel<<<pl->scan_blocks, 1024, 0, pl->stream>>>(
         pl->counts, pl->params, pl->block_pts, pl->block_chunks, pl->tickets + 1);
     scan_boxes_kernel<S, PP><<<pl->scan_blocks, 1024, 0, pl->stream>>>(
         pl->counts, pl->params, pl->block_pts, pl->block_chunks, pl->box_start, pl->cursor,
-        pl->chunk_start, pl->chunk_box, pl->w, pl->N);
-    scatter_kernel<S><<<gp, 1024, hs, pl->stream>>>(Y, pl->N, pl->params, pl->cursor, pl->sorted_y);
+        pl->chunk_start, pl->chunk_box, pl->N);
+    scatter_kernel<S><<<gp, 256, hs, pl->stream>>>(Y, pl->N, pl->params, pl->cursor, pl->sorted_y);
     const int gs = grid_for(pl, pl->chunk_cap * 32, 256, 8);
     spread_kernel<S, PP><<<gs, 256, 0, pl->stream>>>(pl->sorted_y, pl->box_start, pl->chunk_start,
                                                      pl->chunk_box, pl->params, pl->w);
