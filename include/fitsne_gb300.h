@@ -69,6 +69,8 @@ typedef struct {
     int32_t n_int_max; /* cap of the rule and size of the grids [1000 if s = 1, 400 if s = 2];
                           p * n_int_max may not exceed 3000 (s = 1) or 1200 (s = 2) */
     void* stream;      /* cudaStream_t for all work; NULL = the legacy default stream */
+    int32_t relabel_first; /* iteration of a run's first locality relabelling [100]; < 0: never */
+    int32_t relabel_every; /* iterations between later relabellings [300] */
 } tsne_plan_opts;
 
 /* Gradient-descent schedule (Sec. 1.2 early exaggeration, Sec. 4 late
@@ -178,6 +180,15 @@ int tsne_run(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
  * it_begin + count - 1 of the schedule sp on Y (device, in place), keeping
  * uY and gains in the plan between calls. tsne_run equals a reset followed
  * by tsne_run_iters(0, sp->n_iter) (and the optional KL).
+ *
+ * Locality relabelling: at iteration relabel_first and every relabel_every
+ * iterations after it (plan options), a run relabels its points along a
+ * Morton curve of the current embedding (ties by label: deterministic) and
+ * builds the correspondingly relabelled copy of P (plan-owned, allocated on
+ * first use: 8 bytes per stored entry), so that the attraction finds most
+ * neighbours in a shared-memory window of Y. The gradient is unchanged up to
+ * the order of each row's attraction sum; Y is returned in the caller's
+ * labels. P must stay the same across the tsne_run_iters calls of one run.
  */
 int tsne_run_reset(tsne_plan* plan);
 int tsne_run_iters(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,

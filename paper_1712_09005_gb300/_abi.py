@@ -38,7 +38,8 @@ class tsne_csr(ctypes.Structure):
 
 class tsne_plan_opts(ctypes.Structure):
     _fields_ = [("n_min", ctypes.c_int32), ("n_int_max", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("relabel_first", ctypes.c_int32),
+                ("relabel_every", ctypes.c_int32)]
 
 
 class tsne_step_params(ctypes.Structure):

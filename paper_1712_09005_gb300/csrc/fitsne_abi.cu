@@ -140,7 +140,10 @@ void free_plan(tsne_plan* pl) {
                     pl->sorted_y,  pl->w,           pl->spec,        pl->hgrid,      pl->z_partial,
                     pl->kl_partial, pl->kl_out_dev, pl->valid_flag,  pl->y_next,     pl->uY_run,
                     pl->gains_run, pl->fft_table,   pl->twiddles,    pl->h_row_ptr,  pl->h_col,
-                    pl->h_val,     pl->h_Y,         pl->fft_of_n};
+                    pl->h_val,     pl->h_Y,         pl->fft_of_n,    pl->perm,       pl->inv,
+                    pl->perm_next, pl->inv_next,    pl->row_len,     pl->cur_of,     pl->rp2,
+                    pl->col2,      pl->val2,        pl->chunk_sum,   pl->chunk_centre, pl->sort_keys,
+                    pl->scan_bsum, pl->tmp_state,   pl->y_cur};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete pl;
@@ -268,6 +271,8 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     pl->stream = (cudaStream_t)o.stream;
     pl->n_max = p * n_int_max;
     pl->fx_shift = fixed_point_shift(N, s, p);
+    pl->relabel_first = o.relabel_first == 0 ? 100 : o.relabel_first;
+    pl->relabel_every = o.relabel_every > 0 ? o.relabel_every : 300;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -295,7 +300,7 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     if (rc == TSNE_OK) rc = dalloc(&pl->ptr, (size_t)(count), #ptr)
     ALLOC(params, 1);
     ALLOC(box_partial, 2 * fitsne::kBoxBlocks);
-    ALLOC(tickets, 4);
+    ALLOC(tickets, 8);
     ALLOC(counts, pl->n_boxes_max);
     ALLOC(box_start, pl->n_boxes_max + 1);
     ALLOC(cursor, pl->n_boxes_max);
@@ -316,12 +321,28 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     ALLOC(gains_run, N * s);
     ALLOC(fft_table, tab.size());
     ALLOC(fft_of_n, pl->n_max + 1);
+    int64_t Mpow = 1;
+    while (Mpow < N) Mpow <<= 1;
+    const int64_t nchunk = N / fitsne::kForceChunk + 1;
+    ALLOC(perm, N);
+    ALLOC(inv, N);
+    ALLOC(perm_next, N);
+    ALLOC(inv_next, N);
+    ALLOC(row_len, N);
+    ALLOC(cur_of, N);
+    ALLOC(rp2, N + 1);
+    ALLOC(chunk_sum, nchunk);
+    ALLOC(chunk_centre, nchunk);
+    ALLOC(sort_keys, Mpow);
+    ALLOC(scan_bsum, N / 2048 + 1);
+    ALLOC(tmp_state, N * s);
+    ALLOC(y_cur, N * s);
     ALLOC(twiddles, tw_total);
 #undef ALLOC
     if (rc != TSNE_OK) { free_plan(pl); return rc; }
     cudaStream_t st = pl->stream;
     ce = cudaMemsetAsync(pl->params, 0, sizeof(Params), st);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(pl->tickets, 0, 4 * sizeof(unsigned), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(pl->tickets, 0, 8 * sizeof(unsigned), st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(pl->counts, 0, pl->n_boxes_max * sizeof(int32_t), st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(pl->fft_table, tab.data(), tab.size() * sizeof(FftEntry),
@@ -338,6 +359,7 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
         ce = cudaMemcpyAsync(pl->fft_of_n, of_n.data(), of_n.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess) ce = fitsne::fft_configure(pl);
+    if (ce == cudaSuccess) ce = fitsne::force_configure(pl);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { free_plan(pl); return cuda_fail(ce, "plan initialisation"); }
     *out = pl;
@@ -410,23 +432,52 @@ static int reset_run_state(tsne_plan* plan) {
     const int64_t M = plan->N * plan->s;
     CU(cudaMemsetAsync(plan->uY_run, 0, sizeof(float) * M, plan->stream), "uY reset");
     CU(fitsne::launch_fill(plan, plan->gains_run, 1.0f, M), "gains reset");
+    plan->reordered = 0;
     return TSNE_OK;
 }
 
-// Iterations it0 .. it0+count-1, ping-ponging Y with plan scratch; the
-// result ends in Y.
+static bool relabel_at(const tsne_plan* plan, int it) {
+    if (plan->relabel_first < 0 || it < plan->relabel_first) return false;
+    return (it - plan->relabel_first) % plan->relabel_every == 0;
+}
+
+// Relabels the run at the current state (Y in cur, in the current labels):
+// the new-label Y goes to nxt, which becomes the current buffer.
+static int relabel(tsne_plan* plan, const tsne_csr& P, float*& cur, float*& nxt) {
+    if (P.nnz > plan->nnz2_cap) {
+        if (plan->col2) cudaFree(plan->col2);
+        if (plan->val2) cudaFree(plan->val2);
+        plan->col2 = nullptr;
+        plan->val2 = nullptr;
+        plan->nnz2_cap = 0;
+        if (int rc = dalloc(&plan->col2, P.nnz, "relabelled col")) return rc;
+        if (int rc = dalloc(&plan->val2, P.nnz, "relabelled val")) return rc;
+        plan->nnz2_cap = P.nnz;
+    }
+    CU(fitsne::launch_box(plan, cur), "box kernel launch");
+    CU(fitsne::launch_relabel(plan, P, cur, plan->uY_run, plan->gains_run, nxt), "relabel launch");
+    std::swap(cur, nxt);
+    return TSNE_OK;
+}
+
+// Iterations it0 .. it0+count-1, ping-ponging Y between plan buffers; Y (in
+// the caller's labels) holds the input and receives the result.
 static int run_iters(tsne_plan* plan, const tsne_csr& P, float* Y, const tsne_step_params* sp,
                      int it0, int count) {
-    float* cur = Y;
+    const int64_t ns = plan->N * plan->s;
+    float* cur = plan->y_cur;
     float* nxt = plan->y_next;
+    if (plan->reordered) CU(fitsne::launch_to_labels(plan, Y, 0, cur), "Y to run labels");
+    else CU(cudaMemcpyAsync(cur, Y, sizeof(float) * ns, cudaMemcpyDeviceToDevice, plan->stream), "Y copy");
     for (int it = it0; it < it0 + count; ++it) {
-        if (int rc = step_into(plan, P, cur, nxt, plan->uY_run, plan->gains_run, it, sp)) return rc;
+        if (relabel_at(plan, it))
+            if (int rc = relabel(plan, P, cur, nxt)) return rc;
+        const tsne_csr Pr = plan->reordered ? tsne_csr{plan->rp2, plan->col2, plan->val2, P.nnz} : P;
+        if (int rc = step_into(plan, Pr, cur, nxt, plan->uY_run, plan->gains_run, it, sp)) return rc;
         std::swap(cur, nxt);
     }
-    if (cur != Y)
-        CU(cudaMemcpyAsync(Y, cur, sizeof(float) * plan->N * plan->s, cudaMemcpyDeviceToDevice,
-                           plan->stream),
-           "copy of the final Y");
+    if (plan->reordered) CU(fitsne::launch_to_labels(plan, cur, 1, Y), "Y to caller labels");
+    else CU(cudaMemcpyAsync(Y, cur, sizeof(float) * ns, cudaMemcpyDeviceToDevice, plan->stream), "Y copy");
     return TSNE_OK;
 }
 

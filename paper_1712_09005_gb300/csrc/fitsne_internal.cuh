@@ -18,6 +18,10 @@ constexpr int kBoxThreads = 256;  // threads of the bounding-box blocks
 constexpr int kBoxBlocks = 304;   // 2 per SM on 152 SMs
 constexpr int kHistBins = 12288;  // boxes that fit a shared-memory histogram (48 KB)
 constexpr int kSortPts = 2048;    // points per block of the sort kernels (256 threads x 8)
+constexpr int kForceChunk = 256;  // rows per CTA step of the force kernel (8 warps x 32)
+#ifndef FITSNE_WIN_BYTES
+#define FITSNE_WIN_BYTES 98304    // shared-memory window of Y per force CTA (relabelled runs)
+#endif
 
 // One FFT length of the plan's table: L = product of radix[0..nst), each
 // radix in {2, 3, 4, 5}; tw_off locates its L twiddles exp(-2 pi i j / L).
@@ -102,6 +106,25 @@ struct tsne_plan {
     float* gains_run;        // [N * s]
     fitsne::FftEntry* fft_table;
     float2* twiddles;
+    // locality relabelling of a run (fitsne_reorder.cu)
+    int relabel_first, relabel_every;  // iterations at which a run relabels (first < 0: never)
+    int reordered;           // run state and rp2/col2/val2 use the relabelled order
+    int32_t* perm;           // [N] new label -> caller's label
+    int32_t* inv;            // [N] caller's label -> new label
+    int32_t* perm_next;      // [N]
+    int32_t* inv_next;       // [N]
+    int32_t* row_len;        // [N]
+    int32_t* cur_of;         // [N]
+    int32_t* rp2;            // [N + 1] relabelled P
+    int32_t* col2;           // [nnz2_cap]
+    float* val2;             // [nnz2_cap]
+    int64_t nnz2_cap;
+    unsigned long long* chunk_sum;  // [N / kForceChunk + 1]
+    int32_t* chunk_centre;   // [N / kForceChunk + 1] window centre per 256-row chunk
+    unsigned long long* sort_keys;  // [next_pow2(N)]
+    int32_t* scan_bsum;      // [N / 2048 + 1]
+    float* tmp_state;        // [N * s]
+    float* y_cur;            // [N * s] run state Y in the relabelled order
     // host-buffer path (tsne_run_host), allocated on first use
     int64_t host_nnz_cap;
     int32_t* h_row_ptr;
@@ -171,6 +194,13 @@ cudaError_t launch_gradient(tsne_plan* pl, const tsne_csr& P, const float* Y, fl
 cudaError_t launch_step(tsne_plan* pl, const tsne_csr& P, const float* Y, float* Y_new,
                         float* uY, float* gains, float alpha, float momentum, float lr,
                         float min_gain, float gain_inc, float gain_dec);
+// Relabels the run (state Y_cur, uY_cur, gains_cur in the current labels) and
+// builds the relabelled P; the relabelled Y goes to Y_out, uY and gains are
+// moved in place.
+cudaError_t launch_relabel(tsne_plan* pl, const tsne_csr& P, const float* Y_cur, float* uY_cur,
+                           float* gains_cur, float* Y_out);
+// to_caller = 1: dst[perm[k]] = src[k]; 0: dst[k] = src[perm[k]].
+cudaError_t launch_to_labels(tsne_plan* pl, const float* src, int to_caller, float* dst);
 cudaError_t launch_kl(tsne_plan* pl, const tsne_csr& P, const float* Y);
 // KL reduction with explicit scratch: 2 doubles per block in partial, a
 // self-resetting completion counter, Z from Z_dev (device) or Z_val.
@@ -179,6 +209,7 @@ cudaError_t launch_kl_raw(const tsne_csr& P, const float* Y, int64_t N, int s,
                           double* out, int blocks, cudaStream_t stream);
 cudaError_t launch_validate(tsne_plan* pl, const tsne_csr& P);
 cudaError_t launch_fill(tsne_plan* pl, float* a, float v, int64_t n);
-cudaError_t fft_configure(tsne_plan* pl);  // sets shared-memory limits
+cudaError_t fft_configure(tsne_plan* pl);    // sets shared-memory limits
+cudaError_t force_configure(tsne_plan* pl);  // shared-memory limit of the windowed force kernel
 
 }  // namespace fitsne

@@ -12,6 +12,8 @@
 // of boxes holding more than one chunk of points.
 #include <math.h>
 
+#include <algorithm>
+
 #include "fitsne_internal.cuh"
 
 namespace fitsne {
@@ -545,18 +547,31 @@ __device__ __forceinline__ float update_one(float y, float dy, float& u, float& 
 #define FITSNE_GATHER_L2_ONLY 0  // 1: the Y[j] gathers bypass L1 (ld.global.cg)
 #endif
 
-template <int S>
+// y_j from the shared-memory window [w0, w0 + wn) of a relabelled run when it
+// holds j, else from global memory.
+struct Window {
+    const float* s;  // shared copy of Y[w0 .. w0 + wn)
+    int w0, wn;
+};
+
+template <int S, bool WIN>
 __device__ __forceinline__ void attract(float yi0, float yi1, int j, float v,
-                                        const float* __restrict__ Y, float& a0, float& a1) {
+                                        const float* __restrict__ Y, const Window& win,
+                                        float& a0, float& a1) {
+    const unsigned off = (unsigned)(j - win.w0);
+    const bool in = WIN && off < (unsigned)win.wn;
     if (S == 2) {
-        const float2 yj = FITSNE_GATHER_L2_ONLY ? __ldcg(reinterpret_cast<const float2*>(Y) + j)
-                                                : __ldg(reinterpret_cast<const float2*>(Y) + j);
+        float2 yj;
+        if (in) yj = reinterpret_cast<const float2*>(win.s)[off];
+        else yj = FITSNE_GATHER_L2_ONLY ? __ldcg(reinterpret_cast<const float2*>(Y) + j)
+                                        : __ldg(reinterpret_cast<const float2*>(Y) + j);
         const float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
         const float q = __fdividef(v, 1.0f + d0 * d0 + d1 * d1);
         a0 += q * d0;
         a1 += q * d1;
     } else {
-        const float d0 = yi0 - (FITSNE_GATHER_L2_ONLY ? __ldcg(Y + j) : __ldg(Y + j));
+        const float yj = in ? win.s[off] : (FITSNE_GATHER_L2_ONLY ? __ldcg(Y + j) : __ldg(Y + j));
+        const float d0 = yi0 - yj;
         a0 += __fdividef(v, 1.0f + d0 * d0) * d0;
     }
 }
@@ -575,24 +590,29 @@ __device__ __forceinline__ void load_slots(const int32_t* __restrict__ col,
 
 // Attraction of one row from its prefetched entries (and any beyond 32 U),
 // summed over the warp.
-template <int S, int U>
+template <int S, bool WIN, int U>
 __device__ __forceinline__ void attract_row(const int32_t* __restrict__ col,
                                             const float* __restrict__ val,
-                                            const float* __restrict__ Y, int beg, int end,
-                                            float yi0, float yi1, int lane, const int (&jj)[U],
-                                            const float (&vv)[U], float& a0, float& a1) {
+                                            const float* __restrict__ Y, const Window& win,
+                                            int beg, int end, float yi0, float yi1, int lane,
+                                            const int (&jj)[U], const float (&vv)[U], float& a0,
+                                            float& a1) {
     a0 = 0.0f;
     a1 = 0.0f;
 #pragma unroll
     for (int u = 0; u < U; ++u)
-        if (beg + lane + 32 * u < end) attract<S>(yi0, yi1, jj[u], vv[u], Y, a0, a1);
+        if (beg + lane + 32 * u < end) attract<S, WIN>(yi0, yi1, jj[u], vv[u], Y, win, a0, a1);
     for (int e = beg + lane + 32 * U; e < end; e += 32)
-        attract<S>(yi0, yi1, __ldcs(&col[e]), __ldcs(&val[e]), Y, a0, a1);
+        attract<S, WIN>(yi0, yi1, __ldcs(&col[e]), __ldcs(&val[e]), Y, win, a0, a1);
     a0 = warp_sum(a0);
     if (S == 2) a1 = warp_sum(a1);
 }
 
-// Each warp owns blocks of 32 consecutive points (rows of P). Per block:
+// A CTA takes chunks of kForceChunk = 256 consecutive points (rows of P);
+// warp w of the CTA owns rows 32 w .. 32 w + 31 of the chunk. In a relabelled
+// run (WIN) the CTA first copies the window of Y centred on the chunk's mean
+// neighbour label into shared memory, and the attraction reads y_j there
+// when the window holds j. Per 32-row block:
 //  1. lane l takes point i0 + l: its row bounds, coordinates, optimizer state
 //     (coalesced), its box, local coordinates and Lagrange weights, and the
 //     Step 3 interpolation of the node values of its box -> F_rep;
@@ -607,21 +627,39 @@ __device__ __forceinline__ void attract_row(const int32_t* __restrict__ col,
 #define FITSNE_FORCE_MINB 4   // resident 256-thread blocks per SM the registers must allow
 #endif
 
-template <int S, int PP, bool STEP>
-__global__ void __launch_bounds__(256, FITSNE_FORCE_MINB)
+template <int S, int PP, bool STEP, bool WIN>
+__global__ void __launch_bounds__(256, WIN ? 2 : FITSNE_FORCE_MINB)
 force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
              const float* __restrict__ val, const float* __restrict__ Y,
              const Params* __restrict__ params, const float4* __restrict__ hgrid, float alpha,
-             float* __restrict__ dY, StepArgs sa, int64_t N) {
+             float* __restrict__ dY, StepArgs sa, int64_t N,
+             const int32_t* __restrict__ chunk_centre, int win_cap) {
     constexpr int U = FITSNE_FORCE_SLOTS;
+    extern __shared__ float s_win[];
     const Params P = *params;
     if (P.error) return;
     const int lane = threadIdx.x % 32;
-    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
     const float fs = P.delta * P.inv_Z;
     const int n = P.n;
-    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32 * 32; i0 < N;
-         i0 += nwarp * 32) {
+    Window win{s_win, 0, 0};
+    for (int64_t c = blockIdx.x; c * kForceChunk < N; c += gridDim.x) {
+        if (WIN) {
+            __syncthreads();  // the previous chunk's readers are done
+            const int64_t wn = N < win_cap ? N : win_cap;
+            int64_t w0 = (int64_t)chunk_centre[c] - wn / 2;
+            if (w0 > N - wn) w0 = N - wn;
+            if (w0 < 0) w0 = 0;
+            w0 &= ~(int64_t)3;  // 16-byte aligned staging loads
+            win.w0 = (int)w0;
+            win.wn = (int)wn;
+            for (int t = threadIdx.x; t < wn * S / 4; t += blockDim.x)
+                reinterpret_cast<float4*>(s_win)[t] = __ldg(reinterpret_cast<const float4*>(Y + w0 * S) + t);
+            for (int t = (int)(wn * S / 4) * 4 + threadIdx.x; t < wn * S; t += blockDim.x)
+                s_win[t] = __ldg(Y + w0 * S + t);
+            __syncthreads();
+        }
+        const int64_t i0 = c * kForceChunk + (threadIdx.x / 32) * 32;
+        if (i0 >= N) continue;
         const int64_t i = i0 + lane;
         const bool live = i < N;
         const int nrows = (N - i0) < 32 ? (int)(N - i0) : 32;
@@ -695,7 +733,7 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             {
                 const float y0 = __shfl_sync(kFull, yi0, r), y1 = __shfl_sync(kFull, yi1, r);
                 float a0, a1;
-                attract_row<S, U>(col, val, Y, bA, eA, y0, y1, lane, jA, vA, a0, a1);
+                attract_row<S, WIN, U>(col, val, Y, win, bA, eA, y0, y1, lane, jA, vA, a0, a1);
                 if (lane == r) { A0 = a0; A1 = a1; }
             }
             if (hasB) {
@@ -705,7 +743,7 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
                 }
                 const float y0 = __shfl_sync(kFull, yi0, r + 1), y1 = __shfl_sync(kFull, yi1, r + 1);
                 float a0, a1;
-                attract_row<S, U>(col, val, Y, bB, eB, y0, y1, lane, jB, vB, a0, a1);
+                attract_row<S, WIN, U>(col, val, Y, win, bB, eB, y0, y1, lane, jB, vB, a0, a1);
                 if (lane == r + 1) { A0 = a0; A1 = a1; }
             }
         }
@@ -879,25 +917,56 @@ cudaError_t launch_sort_and_spread(tsne_plan* pl, const float* Y) {
     return cudaGetLastError();
 }
 
-template <int S, int PP, bool STEP>
+template <int S, int PP, bool STEP, bool WIN>
 static void force_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha, float* dY,
                        StepArgs sa) {
-    const int g = grid_for(pl, pl->N, 256, 8);
-    force_kernel<S, PP, STEP><<<g, 256, 0, pl->stream>>>(P.row_ptr, P.col, P.val, Y, pl->params,
-                                                         pl->hgrid, alpha, dY, sa, pl->N);
+    if (WIN) {
+        const int64_t nch = (pl->N + kForceChunk - 1) / kForceChunk;
+        const int ctas = (int)std::min<int64_t>(nch, 2LL * pl->sm_count);
+        const int cap = FITSNE_WIN_BYTES / (int)(sizeof(float) * S);
+        force_kernel<S, PP, STEP, true><<<ctas, 256, FITSNE_WIN_BYTES, pl->stream>>>(
+            P.row_ptr, P.col, P.val, Y, pl->params, pl->hgrid, alpha, dY, sa, pl->N,
+            pl->chunk_centre, cap);
+    } else {
+        const int g = grid_for(pl, pl->N, 256, 8);
+        force_kernel<S, PP, STEP, false><<<g, 256, 0, pl->stream>>>(
+            P.row_ptr, P.col, P.val, Y, pl->params, pl->hgrid, alpha, dY, sa, pl->N, nullptr, 0);
+    }
     pl->launches += 1;
 }
 
 template <int S, int PP>
 static void gradient_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,
                           float* dY) {
-    force_impl<S, PP, false>(pl, P, Y, alpha, dY, StepArgs{});
+    force_impl<S, PP, false, false>(pl, P, Y, alpha, dY, StepArgs{});
 }
 
 template <int S, int PP>
 static void step_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,
                       const StepArgs& sa) {
-    force_impl<S, PP, true>(pl, P, Y, alpha, nullptr, sa);
+    if (pl->reordered) force_impl<S, PP, true, true>(pl, P, Y, alpha, nullptr, sa);
+    else force_impl<S, PP, true, false>(pl, P, Y, alpha, nullptr, sa);
+}
+
+template <int S, int PP>
+static cudaError_t configure_impl() {
+    return cudaFuncSetAttribute(force_kernel<S, PP, true, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, FITSNE_WIN_BYTES);
+}
+
+cudaError_t force_configure(tsne_plan* pl) {
+    cudaError_t e = cudaSuccess;
+    switch (pl->p * 10 + pl->s) {
+        case 21: e = configure_impl<1, 2>(); break;
+        case 22: e = configure_impl<2, 2>(); break;
+        case 31: e = configure_impl<1, 3>(); break;
+        case 32: e = configure_impl<2, 3>(); break;
+        case 41: e = configure_impl<1, 4>(); break;
+        case 42: e = configure_impl<2, 4>(); break;
+        case 51: e = configure_impl<1, 5>(); break;
+        default: e = configure_impl<2, 5>(); break;
+    }
+    return e;
 }
 
 cudaError_t launch_gradient(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,

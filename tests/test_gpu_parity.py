@@ -325,3 +325,26 @@ def test_bitwise_reproducible(s):
         b, Zb = plan.gradient(Pd, Yd, alpha=12.0)
         torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(Za, Zb)
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_locality_relabelling(s):
+    """A run that relabels its points (iterations 5, 15, 25) follows the run that
+    does not up to the order of the attraction sums, returns Y in the caller's
+    labels, and is itself bitwise reproducible."""
+    N = 6000
+    P = affinities(N, 11)
+    Y0 = clustered_Y(N, s, 3.0, seed=31)
+    sched = pkg.Schedule(n_iter=30)
+    Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+    out = {}
+    for tag, first in (("plain", -1), ("relabel", 5), ("relabel2", 5)):
+        with pkg.Plan(N, s, relabel_first=first, relabel_every=10) as plan:
+            Y = torch.as_tensor(Y0.copy(), device="cuda")
+            kl = plan.run(Pd, Y, sched)
+            assert plan.status() == 0
+            out[tag] = (kl, Y.cpu().numpy())
+    assert np.array_equal(out["relabel"][1], out["relabel2"][1])
+    assert abs(out["relabel"][0] - out["plain"][0]) <= 1e-3 * out["plain"][0]
+    d = np.linalg.norm(out["relabel"][1] - out["plain"][1]) / np.linalg.norm(out["plain"][1])
+    assert d < 1e-3, d
