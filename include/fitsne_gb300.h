@@ -185,8 +185,8 @@ int tsne_run(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
  * iterations after it (plan options), a run relabels its points along a
  * Morton curve of the current embedding (ties by label: deterministic) and
  * builds the correspondingly relabelled copy of P (plan-owned, allocated on
- * first use: 8 bytes per stored entry), so that the attraction finds most
- * neighbours in a shared-memory window of Y. The gradient is unchanged up to
+ * first use: 8 bytes per stored entry), so that the attraction's reads of
+ * neighbouring y_j hit nearby memory (cache reuse). The gradient is unchanged up to
  * the order of each row's attraction sum; Y is returned in the caller's
  * labels. P must stay the same across the tsne_run_iters calls of one run.
  */

@@ -642,7 +642,14 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
     const float fs = P.delta * P.inv_Z;
     const int n = P.n;
     Window win{s_win, 0, 0};
-    for (int64_t c = blockIdx.x; c * kForceChunk < N; c += gridDim.x) {
+#ifndef FITSNE_FORCE_CONTIG
+#define FITSNE_FORCE_CONTIG 0  // 1: each CTA takes a contiguous range of chunks
+#endif
+    const int64_t nch = (N + kForceChunk - 1) / kForceChunk;
+    const int64_t c_lo = FITSNE_FORCE_CONTIG ? nch * blockIdx.x / gridDim.x : blockIdx.x;
+    const int64_t c_hi = FITSNE_FORCE_CONTIG ? nch * (blockIdx.x + 1) / gridDim.x : nch;
+    const int64_t c_step = FITSNE_FORCE_CONTIG ? 1 : gridDim.x;
+    for (int64_t c = c_lo; c < c_hi; c += c_step) {
         if (WIN) {
             __syncthreads();  // the previous chunk's readers are done
             const int64_t wn = N < win_cap ? N : win_cap;
@@ -941,10 +948,14 @@ static void gradient_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, floa
     force_impl<S, PP, false, false>(pl, P, Y, alpha, dY, StepArgs{});
 }
 
+#ifndef FITSNE_RELABEL_WINDOW
+#define FITSNE_RELABEL_WINDOW 0  // 1: relabelled runs read y_j through a shared-memory window
+#endif
+
 template <int S, int PP>
 static void step_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,
                       const StepArgs& sa) {
-    if (pl->reordered) force_impl<S, PP, true, true>(pl, P, Y, alpha, nullptr, sa);
+    if (pl->reordered && FITSNE_RELABEL_WINDOW) force_impl<S, PP, true, true>(pl, P, Y, alpha, nullptr, sa);
     else force_impl<S, PP, true, false>(pl, P, Y, alpha, nullptr, sa);
 }
 

@@ -2,8 +2,9 @@
 //
 // The attraction reads y_j for every stored p_ij: ~150 random 8-byte reads
 // per point per iteration, each one L1TEX request. Relabelling the points so
-// that neighbours in P get nearby labels lets the force kernel serve most of
-// these reads from a shared-memory copy of a window of Y. Neighbours in P are
+// that neighbours in P get nearby labels turns most of these reads into
+// cache hits of the CTA's working set (and, with the window variant of the
+// force kernel, into shared-memory reads). Neighbours in P are
 // close in the embedding once the clusters have formed, so the new labels
 // follow a Morton (Z-order) curve over a 1024 x 1024 grid on the current
 // box (1-D: 2^20 cells), ties broken by the original label: a deterministic
