@@ -263,6 +263,120 @@ int tsne_plan_profile_read(tsne_plan* plan, double* ms_out, int64_t* count_out);
  * count of every kernel launch the library enqueued for it). */
 int64_t tsne_plan_launch_count(const tsne_plan* plan);
 
+/* ------------------------------------------------------------------------
+ * Batched iterations of many independent embedding jobs.
+ *
+ * The paper's method is one embedding at a time (Algorithm 1 per
+ * iteration); a batch runs the same per-iteration path (box, counting sort,
+ * spread, FFT convolution + Z, attraction + Step 3 + update) for many jobs at
+ * once: every phase is ONE kernel launch whose blocks share out the work
+ * items of all jobs, each job keeping its own P, Y, optimizer state,
+ * bounding box, N_int, node grid and FFT length (decided on the device every
+ * iteration). The launch sequence of one iteration is captured once in a
+ * CUDA graph and replayed, so an iteration of all jobs costs one host call.
+ * Jobs join and leave between iterations: their scratch comes from the
+ * stream-ordered allocator (cudaMallocAsync on the batch's stream), which
+ * never synchronises the device. A job's iterations are bitwise equal to the
+ * same job run alone (no kernel mixes values of different jobs; every
+ * reduction has a fixed order).
+ * ------------------------------------------------------------------------ */
+typedef struct tsne_batch tsne_batch;
+
+/* Batch options; tsne_batch_opts_default fills the defaults in brackets. */
+typedef struct {
+    int32_t n_min;     /* floor of the interval rule [50] (Sec. 2.5) */
+    int32_t n_int_max; /* cap of the rule and size of every job's grids [1000 if s = 1, 400 if s = 2] */
+    int32_t max_jobs;  /* job slots, 1 .. 256 [64] */
+    int32_t use_graph; /* 1: replay one captured CUDA graph per iteration [1]; 0: plain launches */
+    void* stream;      /* cudaStream_t for all work (not the legacy default stream);
+                          NULL: the batch creates its own non-blocking stream */
+} tsne_batch_opts;
+
+/* Interval-count policies (the automatic rule of Sec. 2.5 gives r): */
+#define TSNE_NINT_RULE 0 /* N_int = r */
+#define TSNE_NINT_FILL 1 /* the most intervals whose nodes fit the FFT length r gets (>= r, <= n_int_max) */
+
+/* Tuning of a batch (see tsne_batch_autotune). */
+typedef struct {
+    int32_t chunk;        /* points per spread work item, one warp each: 32, 64, 128 [128] or 256
+                             (a box of c points gets ceil(c / chunk) warps) */
+    int32_t fft_threads;  /* threads per CTA of the 2-D FFT passes: 256, 512, 1024, or 0 [0] for
+                             256 (row passes) / 512 (column pass) */
+    int32_t n_int_policy; /* TSNE_NINT_RULE [default] or TSNE_NINT_FILL */
+    float ms_per_iter;    /* set by tsne_batch_autotune: measured time of one iteration */
+} tsne_batch_tuning;
+
+void tsne_batch_opts_default(tsne_batch_opts* out);
+
+/* Creates an empty batch of jobs in s dimensions (1 or 2) with p nodes per
+ * interval (2..5). Errors: INVALID_ARG, OOM, CUDA. */
+int tsne_batch_create(int32_t s, int32_t p, const tsne_batch_opts* opts, tsne_batch** out);
+
+/* Frees the batch and every job's scratch (synchronises its stream). NULL is a no-op. */
+int tsne_batch_destroy(tsne_batch* batch);
+
+/* Device bytes a job of N points takes in this batch (Y, two Y buffers,
+ * optimizer state and grid scratch; P is the caller's and not counted), or -1. */
+int64_t tsne_batch_job_bytes(const tsne_batch* batch, int64_t N);
+
+/* Device bytes of all jobs now in the batch (sum of tsne_batch_job_bytes). */
+int64_t tsne_batch_bytes_in_use(const tsne_batch* batch);
+
+/*
+ * Adds a job: N points, affinities P (device CSR as in tsne_gradient; the
+ * caller keeps P alive and unchanged until the job is removed), Y0 (device,
+ * [N x s], copied into the job), n_intervals (0 = the automatic rule, else a
+ * fixed N_int <= n_int_max) and the schedule sp (copied; the job runs
+ * iterations 0 .. sp->n_iter - 1 with uY = 0, gains = 1 at the start, exactly
+ * as tsne_run). *job_id receives the job's slot (0 .. max_jobs - 1). Work is
+ * enqueued on the batch's stream. Errors: INVALID_ARG, CAPACITY (no free
+ * slot), OOM, CUDA.
+ */
+int tsne_batch_add_job(tsne_batch* batch, int64_t N, tsne_csr P, const float* Y0,
+                       int32_t n_intervals, const tsne_step_params* sp, int32_t* job_id);
+
+/* Removes a job and returns its scratch to the stream-ordered pool (after the
+ * work already enqueued). Fetch its result first (tsne_batch_get_y). */
+int tsne_batch_remove_job(tsne_batch* batch, int32_t job_id);
+
+/* Enqueues count iterations of every job still inside its schedule (jobs
+ * that finished skip every phase). */
+int tsne_batch_iterate(tsne_batch* batch, int32_t count);
+
+/* Synchronises the batch's stream; for every slot k writes the job's next
+ * iteration index (= iterations done; -1 for a free slot) to iter_out[k] and
+ * its latched device status (TSNE_OK or TSNE_ERR_NONFINITE) to status_out[k]
+ * (HOST arrays of max_jobs entries; either may be NULL). */
+int tsne_batch_poll(tsne_batch* batch, int32_t* iter_out, int32_t* status_out);
+
+/* Enqueues a copy of the job's current Y to Y_out (device, [N x s]). */
+int tsne_batch_get_y(tsne_batch* batch, int32_t job_id, float* Y_out);
+
+/* KL(P || Q) of the job's current Y (as tsne_kl; Z recomputed at that Y).
+ * kl_out is a HOST pointer; synchronises. */
+int tsne_batch_kl(tsne_batch* batch, int32_t job_id, double* kl_out);
+
+/* Sets or reads the tuning used from the next iteration on (every job). */
+int tsne_batch_set_tuning(tsne_batch* batch, const tsne_batch_tuning* t);
+int tsne_batch_get_tuning(const tsne_batch* batch, tsne_batch_tuning* out);
+
+/*
+ * Autotuner: times `iters` iterations of the batch's current jobs under
+ * candidate tunings (coordinate search over chunk in {32, 64, 128, 256}, then
+ * fft_threads in {256, 512, 1024} for s = 2, then TSNE_NINT_FILL, taken when
+ * it costs at most 3 % more, since it only adds intervals), restoring every
+ * job's state after each trial, so the jobs' results do not depend on the
+ * tuning run. Applies the fastest tuning and writes it (with its measured
+ * ms_per_iter) to *out (may be NULL). Synchronises; needs at least one job.
+ */
+int tsne_batch_autotune(tsne_batch* batch, int32_t iters, tsne_batch_tuning* out);
+
+/* Kernels this batch has launched (host-side count). */
+int64_t tsne_batch_launch_count(const tsne_batch* batch);
+
+/* The batch's cudaStream_t. */
+void* tsne_batch_stream(const tsne_batch* batch);
+
 /*
  * KL(P || Q) without any device allocation (the paper has no counterpart;
  * this exists for callers that cannot call cudaMalloc, e.g. a process whose

@@ -22,7 +22,12 @@ __all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destr
            "tsne_plan_set_box", "tsne_gradient", "tsne_step", "tsne_run", "tsne_run_reset", "tsne_run_iters", "tsne_kl",
            "tsne_run_host", "tsne_validate_csr", "tsne_plan_status", "tsne_plan_info",
            "tsne_debug_copy", "tsne_plan_profile", "tsne_plan_profile_read",
-           "tsne_plan_launch_count", "tsne_kl_noalloc", "TsneError"]
+           "tsne_plan_launch_count", "tsne_kl_noalloc", "TsneError", "Batch", "Tuning",
+           "tsne_batch_create", "tsne_batch_destroy", "tsne_batch_job_bytes",
+           "tsne_batch_bytes_in_use", "tsne_batch_add_job", "tsne_batch_remove_job",
+           "tsne_batch_iterate", "tsne_batch_poll", "tsne_batch_get_y", "tsne_batch_kl",
+           "tsne_batch_set_tuning", "tsne_batch_get_tuning", "tsne_batch_autotune",
+           "tsne_batch_launch_count", "tsne_batch_stream"]
 
 
 def lib():
@@ -213,6 +218,191 @@ def tsne_kl_noalloc(P: DeviceCSR, Y: torch.Tensor, s: int, Z: float, kl_out: tor
                                ctypes.c_void_p(stream))
     if rc != 0:
         raise TsneError(rc, lib().tsne_noalloc_last_error_string().decode())
+
+
+# ---- batched jobs ---------------------------------------------------------------
+
+@dataclass
+class Tuning:
+    """tsne_batch_tuning: spread work item, FFT threads per CTA, interval policy."""
+    chunk: int = 128
+    fft_threads: int = 0
+    n_int_policy: int = _abi.TSNE_NINT_RULE
+    ms_per_iter: float = 0.0
+
+    def c(self) -> _abi.tsne_batch_tuning:
+        return _abi.tsne_batch_tuning(self.chunk, self.fft_threads, self.n_int_policy,
+                                      self.ms_per_iter)
+
+    @staticmethod
+    def of(t: _abi.tsne_batch_tuning) -> "Tuning":
+        return Tuning(t.chunk, t.fft_threads, t.n_int_policy, t.ms_per_iter)
+
+
+def tsne_batch_create(s: int, p: int = 3, n_min: int = 0, n_int_max: int = 0, max_jobs: int = 64,
+                      use_graph: bool = True, stream: int | None = None) -> ctypes.c_void_p:
+    opts = _abi.tsne_batch_opts()
+    lib().tsne_batch_opts_default(ctypes.byref(opts))
+    opts.n_min, opts.n_int_max, opts.max_jobs = n_min, n_int_max, max_jobs
+    opts.use_graph = 1 if use_graph else 0
+    opts.stream = stream
+    out = ctypes.c_void_p()
+    check(lib().tsne_batch_create(s, p, ctypes.byref(opts), ctypes.byref(out)))
+    return out
+
+
+def tsne_batch_destroy(batch) -> None:
+    check(lib().tsne_batch_destroy(batch))
+
+
+def tsne_batch_job_bytes(batch, N: int) -> int:
+    return int(lib().tsne_batch_job_bytes(batch, N))
+
+
+def tsne_batch_bytes_in_use(batch) -> int:
+    return int(lib().tsne_batch_bytes_in_use(batch))
+
+
+def tsne_batch_add_job(batch, P: DeviceCSR, Y0: torch.Tensor, sched: Schedule,
+                       n_intervals: int = 0) -> int:
+    sp = sched.c()
+    jid = ctypes.c_int32(-1)
+    check(lib().tsne_batch_add_job(batch, P.N, P.c(), _ptr(Y0), n_intervals, ctypes.byref(sp),
+                                   ctypes.byref(jid)))
+    return jid.value
+
+
+def tsne_batch_remove_job(batch, job: int) -> None:
+    check(lib().tsne_batch_remove_job(batch, job))
+
+
+def tsne_batch_iterate(batch, count: int) -> None:
+    check(lib().tsne_batch_iterate(batch, count))
+
+
+def tsne_batch_poll(batch, max_jobs: int):
+    it = (ctypes.c_int32 * max_jobs)()
+    st = (ctypes.c_int32 * max_jobs)()
+    check(lib().tsne_batch_poll(batch, it, st))
+    return list(it), list(st)
+
+
+def tsne_batch_get_y(batch, job: int, Y_out: torch.Tensor) -> None:
+    check(lib().tsne_batch_get_y(batch, job, _ptr(Y_out)))
+
+
+def tsne_batch_kl(batch, job: int) -> float:
+    kl = ctypes.c_double()
+    check(lib().tsne_batch_kl(batch, job, ctypes.byref(kl)))
+    return kl.value
+
+
+def tsne_batch_set_tuning(batch, t: Tuning) -> None:
+    tc = t.c()
+    check(lib().tsne_batch_set_tuning(batch, ctypes.byref(tc)))
+
+
+def tsne_batch_get_tuning(batch) -> Tuning:
+    tc = _abi.tsne_batch_tuning()
+    check(lib().tsne_batch_get_tuning(batch, ctypes.byref(tc)))
+    return Tuning.of(tc)
+
+
+def tsne_batch_autotune(batch, iters: int = 3) -> Tuning:
+    tc = _abi.tsne_batch_tuning()
+    check(lib().tsne_batch_autotune(batch, iters, ctypes.byref(tc)))
+    return Tuning.of(tc)
+
+
+def tsne_batch_launch_count(batch) -> int:
+    return int(lib().tsne_batch_launch_count(batch))
+
+
+def tsne_batch_stream(batch) -> int:
+    return int(lib().tsne_batch_stream(batch) or 0)
+
+
+class Batch:
+    """Owns a tsne_batch: many embedding jobs iterated together (one launch
+    per phase for all jobs, one CUDA graph per iteration)."""
+
+    def __init__(self, s: int, p: int = 3, n_min: int = 0, n_int_max: int = 0,
+                 max_jobs: int = 64, use_graph: bool = True, stream: int | None = None):
+        self.s, self.max_jobs = s, max_jobs
+        self.handle = tsne_batch_create(s, p, n_min, n_int_max, max_jobs, use_graph, stream)
+        self.N = {}
+        self._P = {}  # the batch reads each job's P until the job is removed
+        self._ext = torch.cuda.ExternalStream(self.stream)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            tsne_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def stream(self) -> int:
+        return tsne_batch_stream(self.handle)
+
+    def job_bytes(self, N: int) -> int:
+        return tsne_batch_job_bytes(self.handle, N)
+
+    def bytes_in_use(self) -> int:
+        return tsne_batch_bytes_in_use(self.handle)
+
+    def add(self, P: DeviceCSR, Y0: torch.Tensor, sched: Schedule, n_intervals: int = 0) -> int:
+        _vec(Y0, P.N, self.s, "Y0")
+        self._ext.wait_stream(torch.cuda.current_stream())  # P and Y0 are ready
+        jid = tsne_batch_add_job(self.handle, P, Y0, sched, n_intervals)
+        self.N[jid] = P.N
+        self._P[jid] = (P, Y0)
+        return jid
+
+    def remove(self, job: int):
+        tsne_batch_remove_job(self.handle, job)
+        self.N.pop(job, None)
+        self._P.pop(job, None)
+
+    def iterate(self, count: int = 1):
+        tsne_batch_iterate(self.handle, count)
+
+    def poll(self):
+        return tsne_batch_poll(self.handle, self.max_jobs)
+
+    def get_y(self, job: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.N[job], self.s), dtype=torch.float32, device="cuda")
+        _vec(out, self.N[job], self.s, "Y_out")
+        self._ext.wait_stream(torch.cuda.current_stream())
+        tsne_batch_get_y(self.handle, job, out)
+        torch.cuda.current_stream().wait_stream(self._ext)
+        return out
+
+    def kl(self, job: int) -> float:
+        return tsne_batch_kl(self.handle, job)
+
+    def set_tuning(self, t: Tuning):
+        tsne_batch_set_tuning(self.handle, t)
+
+    def tuning(self) -> Tuning:
+        return tsne_batch_get_tuning(self.handle)
+
+    def autotune(self, iters: int = 3) -> Tuning:
+        return tsne_batch_autotune(self.handle, iters)
+
+    def launch_count(self) -> int:
+        return tsne_batch_launch_count(self.handle)
 
 
 # ---- convenience object -------------------------------------------------------

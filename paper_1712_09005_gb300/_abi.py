@@ -58,6 +58,21 @@ class tsne_plan_info_t(ctypes.Structure):
                 ("Z", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+TSNE_NINT_RULE = 0
+TSNE_NINT_FILL = 1
+
+
+class tsne_batch_opts(ctypes.Structure):
+    _fields_ = [("n_min", ctypes.c_int32), ("n_int_max", ctypes.c_int32),
+                ("max_jobs", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class tsne_batch_tuning(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int32), ("fft_threads", ctypes.c_int32),
+                ("n_int_policy", ctypes.c_int32), ("ms_per_iter", ctypes.c_float)]
+
+
 # (name, restype, argtypes) for every entry point of include/fitsne_gb300.h
 _P = ctypes.c_void_p
 _SIGNATURES = [
@@ -91,6 +106,27 @@ _SIGNATURES = [
     ("tsne_plan_profile_read", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int64)]),
     ("tsne_plan_launch_count", ctypes.c_int64, [_P]),
+    ("tsne_batch_opts_default", None, [ctypes.POINTER(tsne_batch_opts)]),
+    ("tsne_batch_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(tsne_batch_opts),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    ("tsne_batch_destroy", ctypes.c_int, [_P]),
+    ("tsne_batch_job_bytes", ctypes.c_int64, [_P, ctypes.c_int64]),
+    ("tsne_batch_bytes_in_use", ctypes.c_int64, [_P]),
+    ("tsne_batch_add_job", ctypes.c_int, [_P, ctypes.c_int64, tsne_csr, _P, ctypes.c_int32,
+                                          ctypes.POINTER(tsne_step_params),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    ("tsne_batch_remove_job", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("tsne_batch_iterate", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("tsne_batch_poll", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    ("tsne_batch_get_y", ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    ("tsne_batch_kl", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    ("tsne_batch_set_tuning", ctypes.c_int, [_P, ctypes.POINTER(tsne_batch_tuning)]),
+    ("tsne_batch_get_tuning", ctypes.c_int, [_P, ctypes.POINTER(tsne_batch_tuning)]),
+    ("tsne_batch_autotune", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(tsne_batch_tuning)]),
+    ("tsne_batch_launch_count", ctypes.c_int64, [_P]),
+    ("tsne_batch_stream", ctypes.c_void_p, [_P]),
     ("tsne_kl_noalloc", ctypes.c_int, [tsne_csr, _P, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_double, _P, _P]),
     ("tsne_noalloc_last_error_string", ctypes.c_char_p, []),

@@ -23,7 +23,8 @@
 // spectrum i S_m), so the spectrum of CG is i S_1 - S_2. Outputs are packed
 // the same way: D0 = U1 + i U2 -> (u'_1, u'_2), D1 = V -> v.
 //
-// 2-D passes (one CTA per work item, grid-stride):
+// 2-D passes (one CTA per work item; the items of every job of the table are
+// shared out over a grid-stride loop):
 //   rows_fwd_kernel  FFT along dimension 2 of the n rows of C0, C1, and of
 //                    the rows o1 = 0..n-1 of CK and CG (the rows o1 < 0
 //                    follow by symmetry)
@@ -31,7 +32,7 @@
 //                    split the packed spectra, the Parseval sums of Z,
 //                    multiply, pack, inverse FFT
 //   rows_inv_kernel  inverse FFT of the n needed rows, node values
-// 1-D: conv1d_kernel does the whole convolution in one CTA.
+// 1-D: conv1d_kernel does a job's whole convolution in one CTA.
 #include <math.h>
 
 #include <algorithm>
@@ -182,28 +183,52 @@ __device__ __forceinline__ int circ_offset(int i, int n, int L) {
 
 }  // namespace
 
+namespace {
+
+__device__ __forceinline__ int fft_rows_items(const Job& J) {
+    const Params* P = J.params;
+    return job_live(*P) ? 4 * P->n : 0;
+}
+__device__ __forceinline__ int fft_cols_items(const Job& J) {
+    const Params* P = J.params;
+    return job_live(*P) ? P->L / 2 + 1 : 0;
+}
+__device__ __forceinline__ int fft_inv_items(const Job& J) {
+    const Params* P = J.params;
+    return job_live(*P) ? P->n : 0;
+}
+__device__ __forceinline__ int fft_1d_items(const Job& J) {
+    const Params* P = J.params;
+    return job_live(*P) ? 1 : 0;
+}
+
+}  // namespace
+
 // ----------------------------------------------------------------------------
-// 2-D, pass 1: row FFTs. Work item m < 4n: type m / n (0: C0, 1: C1, 2: CK,
-// 3: CG), row r = m % n (for CK and CG the offset o1 = r >= 0). Output rows of
-// length L, row-major, at spec + type n L.
+// 2-D, pass 1: row FFTs. Work item m < 4n of a job: type m / n (0: C0, 1: C1,
+// 2: CK, 3: CG), row r = m % n (for CK and CG the offset o1 = r >= 0). Output
+// rows of length L, row-major, at spec + type n L.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-rows_fwd_kernel(const long long* __restrict__ w, const Params* __restrict__ params,
-                const FftEntry* __restrict__ table, const float2* __restrict__ tw_all,
-                float2* __restrict__ spec) {
+__global__ void __launch_bounds__(1024)
+rows_fwd_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
     extern __shared__ float2 sm[];
+    __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ FftEntry e;
-    const Params P = *params;
-    if (P.error) return;
-    if (threadIdx.x == 0) e = table[P.fft_idx];
-    __syncthreads();
-    const int n = P.n, L = P.L;
-    const int64_t G = (int64_t)n * n;
-    const float2* tw = tw_all + e.tw_off;
-    const float inv = P.fx_inv;
-    float2* A = sm;
-    float2* B = sm + L;
-    for (int m = blockIdx.x; m < 4 * n; m += gridDim.x) {
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_rows_items(J); });
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = job_of(s_start, njobs, item);
+        const Job& J = jobs[j];
+        const int m = item - s_start[j];
+        const Params P = *J.params;
+        if (threadIdx.x == 0) e = tab.fft[P.fft_idx];
+        __syncthreads();
+        const int n = P.n, L = P.L;
+        const int64_t G = (int64_t)n * n;
+        const long long* __restrict__ w = J.w;
+        const float2* tw = tab.tw + e.tw_off;
+        const float inv = P.fx_inv;
+        float2* A = sm;
+        float2* B = sm + L;
         const int type = m / n, r = m - type * n;
         for (int c = threadIdx.x; c < L; c += blockDim.x) {
             float2 v = make_float2(0.0f, 0.0f);
@@ -227,7 +252,7 @@ rows_fwd_kernel(const long long* __restrict__ w, const Params* __restrict__ para
         }
         __syncthreads();
         const float2* res = fft_batch(A, B, e, 1, tw, -1.0f);
-        float2* dst = spec + (int64_t)type * n * L + (int64_t)r * L;
+        float2* dst = J.spec + (int64_t)type * n * L + (int64_t)r * L;
         for (int c = threadIdx.x; c < L; c += blockDim.x) dst[c] = res[c];
         __syncthreads();
     }
@@ -248,47 +273,48 @@ __device__ __forceinline__ double block_sum_d(double v, double* sred) {
 
 // Publishes Z = sum_i h1(y_i) - N given S = sum_i h1(y_i) = w0 . (K1 * w0)
 // (equal: both are the sum of L_g(y_i) v1[g] over points and nodes).
-__device__ void publish_Z(double S, Params* params, double* Z_out, int64_t N) {
-    const double Z = S - (double)N;
-    params->Z = Z;
-    params->inv_Z = (float)(1.0 / Z);
-    if (Z_out) *Z_out = Z;
+__device__ void publish_Z(double S, const Job& J) {
+    const double Z = S - (double)J.N;
+    J.params->Z = Z;
+    J.params->inv_Z = (float)(1.0 / Z);
+    if (J.Z_out) *J.Z_out = Z;
 }
 
 // ----------------------------------------------------------------------------
-// 2-D, pass 2: column pairs (k2, L - k2), k2 = 0 .. L/2. Forward FFT of six
-// columns (C0 and C1 at k2 and L - k2, CK and CG at k2), spectra products,
-// inverse FFT of the four packed results, which overwrite the first n rows of
-// columns k2 and L - k2 of C0 and C1.
+// 2-D, pass 2: column pairs (k2, L - k2), k2 = 0 .. L/2 of a job. Forward FFT
+// of six columns (C0 and C1 at k2 and L - k2, CK and CG at k2), spectra
+// products, inverse FFT of the four packed results, which overwrite the first
+// n rows of columns k2 and L - k2 of C0 and C1. The last item of a job sums
+// the Parseval terms into Z.
 // Rows o1 < 0 of the kernels: CK row -r = CK row r (even); the CG row
 // spectrum is real with X_{-r}[k2] = -X_r[L - k2] (G_1 odd, G_2 even in o1).
 // At column L - k2 the kernel spectra are K^(k1, k2), S_1(k1, k2) and
 // -S_2(k1, k2) (G_2 is odd in o2).
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(512)
-cols_kernel(Params* params, const FftEntry* __restrict__ table,
-            const float2* __restrict__ tw_all, float2* __restrict__ spec,
-            double* __restrict__ z_partial, unsigned* __restrict__ ticket, double* Z_out,
-            int64_t N) {
+__global__ void __launch_bounds__(1024)
+cols_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
     extern __shared__ float2 sm[];
+    __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ FftEntry e;
     __shared__ double sred[32];
     __shared__ bool s_last;
-    const Params P = *params;
-    if (P.error) goto done;
-    if (threadIdx.x == 0) e = table[P.fft_idx];
-    __syncthreads();
-    {
-    const int n = P.n, L = P.L;
-    const float2* tw = tw_all + e.tw_off;
-    float2* C0 = spec;
-    float2* C1 = spec + (int64_t)n * L;
-    const float2* CK = spec + 2 * (int64_t)n * L;
-    const float2* CG = spec + 3 * (int64_t)n * L;
-    float2* X = sm;
-    float2* Yb = sm + 6 * L;
-    const float2 z = make_float2(0.0f, 0.0f);
-    for (int k2 = blockIdx.x; k2 <= L / 2; k2 += gridDim.x) {
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_cols_items(J); });
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = job_of(s_start, njobs, item);
+        const Job& J = jobs[j];
+        const int k2 = item - s_start[j], nk = s_start[j + 1] - s_start[j];
+        const Params P = *J.params;
+        if (threadIdx.x == 0) e = tab.fft[P.fft_idx];
+        __syncthreads();
+        const int n = P.n, L = P.L;
+        const float2* tw = tab.tw + e.tw_off;
+        float2* C0 = J.spec;
+        float2* C1 = J.spec + (int64_t)n * L;
+        const float2* CK = J.spec + 2 * (int64_t)n * L;
+        const float2* CG = J.spec + 3 * (int64_t)n * L;
+        float2* X = sm;
+        float2* Yb = sm + 6 * L;
+        const float2 z = make_float2(0.0f, 0.0f);
         const int k2b = (L - k2) % L;
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
             const bool in = i < n;
@@ -342,7 +368,7 @@ cols_kernel(Params* params, const FftEntry* __restrict__ table,
             O[3 * L + k1] = vb;
         }
         const double zt = block_sum_d(zp, sred);
-        if (threadIdx.x == 0) z_partial[k2] = zt;
+        if (threadIdx.x == 0) J.z_partial[k2] = zt;
         __syncthreads();
         const float2* R = fft_batch(O, F, e, 4, tw, 1.0f);
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -353,22 +379,19 @@ cols_kernel(Params* params, const FftEntry* __restrict__ table,
                 C1[(int64_t)i * L + k2b] = R[3 * L + i];
             }
         }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = (atomicAdd(&J.tickets[2], 1u) == (unsigned)nk - 1);
+        }
         __syncthreads();
-    }
-    }
-done:
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    __threadfence();
-    *ticket = 0u;
-    if (!P.error) {
-        double S = 0.0;
-        for (int k2 = 0; k2 <= P.L / 2; ++k2) S += __ldcg(&z_partial[k2]);
-        publish_Z(S / ((double)P.L * (double)P.L), params, Z_out, N);
+        if (s_last && threadIdx.x == 0) {
+            __threadfence();
+            J.tickets[2] = 0u;
+            double S = 0.0;
+            for (int q = 0; q <= L / 2; ++q) S += __ldcg(&J.z_partial[q]);
+            publish_Z(S / ((double)L * (double)L), J);
+        }
+        __syncthreads();
     }
 }
 
@@ -376,24 +399,27 @@ done:
 // 2-D, pass 3: inverse row FFTs of the first n rows of D0 and D1; node
 // values (0, u'_1, u'_2, v) / L^2 for columns < n.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-rows_inv_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ table,
-                const float2* __restrict__ tw_all, const float2* __restrict__ spec,
-                float4* __restrict__ hgrid) {
+__global__ void __launch_bounds__(1024)
+rows_inv_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
     extern __shared__ float2 sm[];
+    __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ FftEntry e;
-    const Params P = *params;
-    if (P.error) return;
-    const int n = P.n, L = P.L;
-    if (threadIdx.x == 0) e = table[P.fft_idx];
-    __syncthreads();
-    const float2* tw = tw_all + e.tw_off;
-    const float2* D0 = spec;
-    const float2* D1 = spec + (int64_t)n * L;
-    float2* X = sm;
-    float2* Yb = sm + 2 * L;
-    const float scale = 1.0f / ((float)L * (float)L);
-    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_inv_items(J); });
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = job_of(s_start, njobs, item);
+        const Job& J = jobs[j];
+        const int r = item - s_start[j];
+        const Params P = *J.params;
+        if (threadIdx.x == 0) e = tab.fft[P.fft_idx];
+        __syncthreads();
+        const int n = P.n, L = P.L;
+        const float2* tw = tab.tw + e.tw_off;
+        const float2* D0 = J.spec;
+        const float2* D1 = J.spec + (int64_t)n * L;
+        float4* __restrict__ hgrid = J.hgrid;
+        float2* X = sm;
+        float2* Yb = sm + 2 * L;
+        const float scale = 1.0f / ((float)L * (float)L);
         for (int c = threadIdx.x; c < L; c += blockDim.x) {
             X[c] = D0[(int64_t)r * L + c];
             X[L + c] = D1[(int64_t)r * L + c];
@@ -409,7 +435,7 @@ rows_inv_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ 
 }
 
 // ----------------------------------------------------------------------------
-// 1-D: the whole convolution in one CTA. Forward: C0 = w0 + i d_1 and
+// 1-D: the whole convolution of a job in one work item. Forward: C0 = w0 + i d_1 and
 // CK' = (K1 + lam G_1) + i K2, lam a power of two (exact) that brings the
 // largest |G_1(o)| = max o / (1 + delta^2 o^2)^2 near 1 (the maximum is
 // 3 sqrt(3) / (16 delta) at o = 1 / (delta sqrt 3), or at o = n - 1), so the
@@ -420,108 +446,118 @@ rows_inv_kernel(const Params* __restrict__ params, const FftEntry* __restrict__ 
 // D0 = U1 + i V -> (u'_1, v). Node values (0, u'_1, 0, v) / L.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-conv1d_kernel(const long long* __restrict__ w, Params* params, const FftEntry* __restrict__ table,
-              const float2* __restrict__ tw_all, float4* __restrict__ hgrid, double* Z_out,
-              int64_t N) {
+conv1d_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
     extern __shared__ float2 sm[];
+    __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ FftEntry e;
     __shared__ double sred[32];
-    const Params P = *params;
-    if (P.error) return;
-    if (threadIdx.x == 0) e = table[P.fft_idx];
-    __syncthreads();
-    const int n = P.n, L = P.L;
-    const float2* tw = tw_all + e.tw_off;
-    const float inv = P.fx_inv;
-    const float o_star = 1.0f / (P.delta * 1.7320508f);
-    const float o_max = (float)(n - 1);
-    const float om = fminf(o_star, o_max);
-    const float den = 1.0f + P.delta2 * om * om;
-    const float g_max = fmaxf(om / (den * den), 1.0f);
-    const int lg = (int)rintf(log2f(g_max));
-    const float lam = ldexpf(1.0f, -lg), inv_lam = ldexpf(1.0f, lg);
-    float2* X = sm;
-    float2* Yb = sm + 2 * L;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        X[i] = i < n ? make_float2(fx(w[i], inv), fx(w[n + i], inv)) : make_float2(0.0f, 0.0f);
-        const int o = circ_offset(i, n, L);
-        float2 kv = make_float2(0.0f, 0.0f);
-        if (o >= 0) {
-            const float2 k = kernel_pair(P.delta2, o * o);
-            const int so = (i < n) ? i : i - L;  // signed offset
-            kv = make_float2(k.x + lam * (float)so * k.y, k.y);
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_1d_items(J); });
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = job_of(s_start, njobs, item);
+        const Job& J = jobs[j];
+        const Params P = *J.params;
+        if (threadIdx.x == 0) e = tab.fft[P.fft_idx];
+        __syncthreads();
+        const int n = P.n, L = P.L;
+        const float2* tw = tab.tw + e.tw_off;
+        const long long* __restrict__ w = J.w;
+        const float inv = P.fx_inv;
+        const float o_star = 1.0f / (P.delta * 1.7320508f);
+        const float o_max = (float)(n - 1);
+        const float om = fminf(o_star, o_max);
+        const float den = 1.0f + P.delta2 * om * om;
+        const float g_max = fmaxf(om / (den * den), 1.0f);
+        const int lg = (int)rintf(log2f(g_max));
+        const float lam = ldexpf(1.0f, -lg), inv_lam = ldexpf(1.0f, lg);
+        float2* X = sm;
+        float2* Yb = sm + 2 * L;
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            X[i] = i < n ? make_float2(fx(w[i], inv), fx(w[n + i], inv)) : make_float2(0.0f, 0.0f);
+            const int o = circ_offset(i, n, L);
+            float2 kv = make_float2(0.0f, 0.0f);
+            if (o >= 0) {
+                const float2 k = kernel_pair(P.delta2, o * o);
+                const int so = (i < n) ? i : i - L;  // signed offset
+                kv = make_float2(k.x + lam * (float)so * k.y, k.y);
+            }
+            X[L + i] = kv;
         }
-        X[L + i] = kv;
+        __syncthreads();
+        float2* F = fft_batch(X, Yb, e, 2, tw, -1.0f);
+        float2* O = (F == X) ? Yb : X;
+        double zp = 0.0;
+        for (int k = threadIdx.x; k < L; k += blockDim.x) {
+            const int kn = (L - k) % L;
+            const float2 x = F[k], xm = conjf2(F[kn]);
+            const float2 w0 = cscale(cadd(x, xm), 0.5f);
+            const float2 t = csub(x, xm);
+            const float2 d1 = make_float2(0.5f * t.y, -0.5f * t.x);
+            const float2 ck = F[L + k], ckn = F[L + kn];
+            const float K1 = ck.x, K2 = 0.5f * (ck.y + ckn.y), S1 = 0.5f * (ck.y - ckn.y) * inv_lam;
+            zp += ((double)w0.x * w0.x + (double)w0.y * w0.y) * (double)K1;
+            const float2 u1 = csub(cscale(d1, K2), mul_si(w0, S1));
+            O[k] = cadd(u1, mul_si(cscale(w0, K2), 1.0f));
+        }
+        const double zt = block_sum_d(zp, sred);
+        if (threadIdx.x == 0) publish_Z(zt / (double)L, J);
+        __syncthreads();
+        const float2* R = fft_batch(O, F, e, 1, tw, 1.0f);
+        const float scale = 1.0f / (float)L;
+        float4* __restrict__ hgrid = J.hgrid;
+        for (int g = threadIdx.x; g < n; g += blockDim.x)
+            hgrid[g] = make_float4(0.0f, R[g].x * scale, 0.0f, R[g].y * scale);
+        __syncthreads();
     }
-    __syncthreads();
-    float2* F = fft_batch(X, Yb, e, 2, tw, -1.0f);
-    float2* O = (F == X) ? Yb : X;
-    double zp = 0.0;
-    for (int k = threadIdx.x; k < L; k += blockDim.x) {
-        const int kn = (L - k) % L;
-        const float2 x = F[k], xm = conjf2(F[kn]);
-        const float2 w0 = cscale(cadd(x, xm), 0.5f);
-        const float2 t = csub(x, xm);
-        const float2 d1 = make_float2(0.5f * t.y, -0.5f * t.x);
-        const float2 ck = F[L + k], ckn = F[L + kn];
-        const float K1 = ck.x, K2 = 0.5f * (ck.y + ckn.y), S1 = 0.5f * (ck.y - ckn.y) * inv_lam;
-        zp += ((double)w0.x * w0.x + (double)w0.y * w0.y) * (double)K1;
-        const float2 u1 = csub(cscale(d1, K2), mul_si(w0, S1));
-        O[k] = cadd(u1, mul_si(cscale(w0, K2), 1.0f));
-    }
-    const double zt = block_sum_d(zp, sred);
-    if (threadIdx.x == 0) publish_Z(zt / (double)L, params, Z_out, N);
-    __syncthreads();
-    const float2* R = fft_batch(O, F, e, 1, tw, 1.0f);
-    const float scale = 1.0f / (float)L;
-    for (int g = threadIdx.x; g < n; g += blockDim.x)
-        hgrid[g] = make_float4(0.0f, R[g].x * scale, 0.0f, R[g].y * scale);
 }
 
 // ----------------------------------------------------------------------------
-// Launch geometry depends only on the plan's capacities, so one enqueued
-// sequence serves every iteration whatever N_int the box rule picks.
+// Launch geometry depends only on the table's capacities, so one enqueued
+// sequence (or a captured graph of it) serves every iteration whatever N_int
+// the box rule picks.
 // ----------------------------------------------------------------------------
-static size_t smem_rows_fwd(const tsne_plan* pl) { return sizeof(float2) * 2 * pl->L_max; }
-static size_t smem_cols(const tsne_plan* pl) { return sizeof(float2) * 12 * pl->L_max; }
-static size_t smem_rows_inv(const tsne_plan* pl) { return sizeof(float2) * 4 * pl->L_max; }
-static size_t smem_1d(const tsne_plan* pl) { return sizeof(float2) * 4 * pl->L_max; }
+static size_t smem_rows_fwd(int L_max) { return sizeof(float2) * 2 * L_max; }
+static size_t smem_cols(int L_max) { return sizeof(float2) * 12 * L_max; }
+static size_t smem_rows_inv(int L_max) { return sizeof(float2) * 4 * L_max; }
+static size_t smem_1d(int L_max) { return sizeof(float2) * 4 * L_max; }
 
-cudaError_t fft_configure(tsne_plan* pl) {
+cudaError_t fft_configure(int s, int L_max) {
     cudaError_t e = cudaSuccess;
-    if (pl->s == 2) {
+    if (s == 2) {
         e = cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_rows_fwd(pl));
+                                 (int)smem_rows_fwd(L_max));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_cols(pl));
+                                     (int)smem_cols(L_max));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_rows_inv(pl));
+                                     (int)smem_rows_inv(L_max));
     } else {
         e = cudaFuncSetAttribute(conv1d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_1d(pl));
+                                 (int)smem_1d(L_max));
     }
     return e;
 }
 
-cudaError_t launch_convolution(tsne_plan* pl, double* Z_out) {
-    if (pl->s == 2) {
-        const int g1 = (int)std::min<int64_t>(4 * (int64_t)pl->n_max, 4 * pl->sm_count);
-        rows_fwd_kernel<<<g1, 256, smem_rows_fwd(pl), pl->stream>>>(pl->w, pl->params, pl->fft_table,
-                                                                     pl->twiddles, pl->spec);
-        const int g2 = (int)std::min<int64_t>(pl->L_max / 2 + 1, 2 * pl->sm_count);
-        cols_kernel<<<g2, 512, smem_cols(pl), pl->stream>>>(pl->params, pl->fft_table, pl->twiddles,
-                                                            pl->spec, pl->z_partial,
-                                                            pl->tickets + 2, Z_out, pl->N);
-        const int g3 = (int)std::min<int64_t>(pl->n_max, 4 * pl->sm_count);
-        rows_inv_kernel<<<g3, 256, smem_rows_inv(pl), pl->stream>>>(
-            pl->params, pl->fft_table, pl->twiddles, pl->spec, pl->hgrid);
-        pl->launches += 3;
+static int cap_grid(int64_t items, int64_t cap) {
+    if (items > cap) items = cap;
+    return (int)(items < 1 ? 1 : items);
+}
+
+cudaError_t launch_convolution(const Job* jobs, const TableCaps& c, const Tables& t,
+                               cudaStream_t st) {
+    const int64_t J = c.njobs;
+    if (c.s == 2) {
+        const int tr = c.fft_threads > 0 ? c.fft_threads : 256;
+        const int tc = c.fft_threads > 0 ? c.fft_threads : 512;
+        const int g1 = cap_grid(4 * (int64_t)c.max_n * J, 4LL * c.sm_count);
+        rows_fwd_kernel<<<g1, tr, smem_rows_fwd(c.max_L), st>>>(jobs, c.njobs, t);
+        const int g2 = cap_grid((int64_t)(c.max_L / 2 + 1) * J, 2LL * c.sm_count);
+        cols_kernel<<<g2, tc, smem_cols(c.max_L), st>>>(jobs, c.njobs, t);
+        const int g3 = cap_grid((int64_t)c.max_n * J, 4LL * c.sm_count);
+        rows_inv_kernel<<<g3, tr, smem_rows_inv(c.max_L), st>>>(jobs, c.njobs, t);
     } else {
-        conv1d_kernel<<<1, 1024, smem_1d(pl), pl->stream>>>(pl->w, pl->params, pl->fft_table,
-                                                            pl->twiddles, pl->hgrid, Z_out, pl->N);
-        pl->launches += 1;
+        const int g = cap_grid(J, c.sm_count);
+        conv1d_kernel<<<g, 1024, smem_1d(c.max_L), st>>>(jobs, c.njobs, t);
     }
     return cudaGetLastError();
 }

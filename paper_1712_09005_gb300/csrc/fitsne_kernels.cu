@@ -1,5 +1,8 @@
-// Per-point and per-entry kernels of the FIt-SNE gradient on sm_103a:
-//   box_kernel      bounding box and interval rule (Sec. 2.2, 2.4, 2.5)
+// Per-point and per-entry kernels of the FIt-SNE gradient on sm_103a, in
+// job-table form (every launch serves all jobs of a table; see
+// fitsne_internal.cuh):
+//   box_kernel      bounding box, interval rule and schedule values
+//                   (Sec. 2.2, 2.4, 2.5; Sec. 1.2 and Sec. 4 exaggeration)
 //   count/scatter   counting sort of the points by box (the "points in I_l"
 //                   loops of Algorithm 1)
 //   scan kernels    box offsets and the spread work list
@@ -7,9 +10,9 @@
 //   force_kernel    attraction over the CSR rows (Sec. 3) fused with Step 3
 //                   (interpolate back), the Appendix assembly of F_rep and,
 //                   for a descent step, the gains/momentum update
+//   advance_kernel  moves each stepping job to its next iteration
 //   kl_kernel       KL(P || Q) of Sec. 1.1 with FP64 sums
-// None of these kernels uses global floating-point atomics except the spread
-// of boxes holding more than one chunk of points.
+// No kernel uses floating-point atomics: the spread sums are integers.
 #include <math.h>
 
 #include <algorithm>
@@ -66,132 +69,185 @@ __device__ __forceinline__ int box_of(const float* __restrict__ Y, int64_t i, co
     }
 }
 
+__device__ __forceinline__ bool schedule_active(const Job& J, int ignore_schedule) {
+    return ignore_schedule || J.mode == kModeGradient || J.dyn->iter < J.iter_end;
+}
+
+// Bounding-box work items of a job: one per 1024 coordinates, at most kBoxBlocks.
+__device__ __forceinline__ int box_items(const Job& J, int s, int ignore_schedule) {
+    if (!schedule_active(J, ignore_schedule)) return 1;
+    const int64_t c = (J.N * s + 1023) / 1024;
+    return (int)(c < 1 ? 1 : (c > kBoxBlocks ? kBoxBlocks : c));
+}
+
+__device__ __forceinline__ int sort_items(const Job& J) {
+    const Params* P = J.params;
+    return job_live(*P) ? (int)((J.N + kSortPts - 1) / kSortPts) : 0;
+}
+
+__device__ __forceinline__ int scan_items(const Job& J) {
+    const Params* P = J.params;
+    return job_live(*P) ? (P->n_boxes + kScanBlock - 1) / kScanBlock : 0;
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------------------
-// Bounding box: per-block min/max, then the last block to finish derives the
-// box, N_int, node spacing and FFT length (Sec. 2.2, 2.4, 2.5). The FP32
-// rule matches the oracle's bit for bit.
+// Bounding box: per-item min/max, then the last item of a job to finish
+// derives the box, N_int, node spacing, FFT length and the iteration's
+// schedule values (Sec. 2.2, 2.4, 2.5). The FP32 rule matches the oracle's
+// bit for bit. A job past its schedule gets one item that marks it inactive.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBoxThreads)
-box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_fixed, int n_min,
-           int n_int_max, int force, float f_y_min, float f_width, int f_n_int, int fx_shift,
-           float* __restrict__ partial, unsigned* __restrict__ ticket, Params* __restrict__ params,
-           const FftEntry* __restrict__ table, const int32_t* __restrict__ fft_of_n) {
-    float lo = INFINITY, hi = -INFINITY;
-    int bad = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if ((reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
-        const int64_t n4 = count / 4;
-        const float4* Y4 = reinterpret_cast<const float4*>(Y);
-        for (int64_t k = k0; k < n4; k += stride) {
-            float4 v = __ldg(&Y4[k]);
-            bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
-            lo = fminf(lo, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
-            hi = fmaxf(hi, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
-        }
-        for (int64_t k = n4 * 4 + k0; k < count; k += stride) {
-            float v = Y[k];
-            bad |= !isfinite(v);
-            lo = fminf(lo, v);
-            hi = fmaxf(hi, v);
-        }
-    } else {
-        for (int64_t k = k0; k < count; k += stride) {
-            float v = Y[k];
-            bad |= !isfinite(v);
-            lo = fminf(lo, v);
-            hi = fmaxf(hi, v);
-        }
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
-        hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
-    }
+box_kernel(const Job* __restrict__ jobs, int njobs, int s, int p, int ignore_schedule,
+           Tables tab) {
+    __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ float s_lo[kBoxThreads / 32], s_hi[kBoxThreads / 32];
     __shared__ bool s_last;
-    bad = __syncthreads_or(bad);
+    const int total = split_jobs(jobs, njobs, s_start,
+                                 [&](const Job& J) { return box_items(J, s, ignore_schedule); });
     const int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < kBoxThreads / 32; ++i) { lo = fminf(lo, s_lo[i]); hi = fmaxf(hi, s_hi[i]); }
-        partial[2 * blockIdx.x] = bad ? NAN : lo;
-        partial[2 * blockIdx.x + 1] = hi;
-        __threadfence();
-        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // the last block reduces the per-block partials
-    int bad_p = 0;
-    lo = INFINITY;
-    hi = -INFINITY;
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
-        float a = __ldcg(&partial[2 * i]), b = __ldcg(&partial[2 * i + 1]);
-        bad_p |= isnan(a);
-        lo = fminf(lo, a);
-        hi = fmaxf(hi, b);
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
-        hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
-    }
-    const bool any_bad = __syncthreads_or(bad_p);
-    if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    for (int i = 0; i < kBoxThreads / 32; ++i) { lo = fminf(lo, s_lo[i]); hi = fmaxf(hi, s_hi[i]); }
-    *ticket = 0u;
-    Params P;
-    P.error = __ldcg(&params->error);
-    if (any_bad) { P.error = TSNE_ERR_NONFINITE; lo = 0.0f; hi = 1.0f; }
-    float y_min, width;
-    int n_int;
-    if (force) {
-        y_min = f_y_min;
-        width = f_width;
-        n_int = f_n_int;
-    } else {
-        y_min = lo;
-        width = __fsub_rn(hi, lo);
-        if (!(width > 0.0f)) width = 1.0f;
-        if (n_int_fixed > 0) {
-            n_int = n_int_fixed;
-        } else {
-            float c = ceilf(width);
-            if (c > (float)n_int_max) c = (float)n_int_max;
-            n_int = (int)c;
-            if (n_int < n_min) n_int = n_min;
-            if (n_int > n_int_max) n_int = n_int_max;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = job_of(s_start, njobs, item);
+        const Job& J = jobs[j];
+        const int k = item - s_start[j], nk = s_start[j + 1] - s_start[j];
+        if (!schedule_active(J, ignore_schedule)) {
+            if (threadIdx.x == 0) J.params->active = 0;
+            continue;  // uniform over the block
         }
+        const int cur = J.dyn->cur;
+        const float* __restrict__ Y = J.ybuf[cur];
+        const int64_t count = J.N * s;
+        float lo = INFINITY, hi = -INFINITY;
+        int bad = 0;
+        const int64_t stride = (int64_t)nk * blockDim.x;
+        const int64_t k0 = (int64_t)k * blockDim.x + threadIdx.x;
+        if ((reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
+            const int64_t n4 = count / 4;
+            const float4* Y4 = reinterpret_cast<const float4*>(Y);
+            for (int64_t q = k0; q < n4; q += stride) {
+                float4 v = __ldg(&Y4[q]);
+                bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
+                lo = fminf(lo, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
+                hi = fmaxf(hi, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+            }
+            for (int64_t q = n4 * 4 + k0; q < count; q += stride) {
+                float v = Y[q];
+                bad |= !isfinite(v);
+                lo = fminf(lo, v);
+                hi = fmaxf(hi, v);
+            }
+        } else {
+            for (int64_t q = k0; q < count; q += stride) {
+                float v = Y[q];
+                bad |= !isfinite(v);
+                lo = fminf(lo, v);
+                hi = fmaxf(hi, v);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+        }
+        bad = __syncthreads_or(bad);
+        if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 1; i < kBoxThreads / 32; ++i) { lo = fminf(lo, s_lo[i]); hi = fmaxf(hi, s_hi[i]); }
+            J.box_partial[2 * k] = bad ? NAN : lo;
+            J.box_partial[2 * k + 1] = hi;
+            __threadfence();
+            s_last = (atomicAdd(&J.tickets[0], 1u) == (unsigned)nk - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            // the last item of the job reduces the job's partials
+            int bad_p = 0;
+            lo = INFINITY;
+            hi = -INFINITY;
+            for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+                float a = __ldcg(&J.box_partial[2 * i]), b = __ldcg(&J.box_partial[2 * i + 1]);
+                bad_p |= isnan(a);
+                lo = fminf(lo, a);
+                hi = fmaxf(hi, b);
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+                hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+            }
+            const bool any_bad = __syncthreads_or(bad_p);
+            if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int i = 0; i < kBoxThreads / 32; ++i) { lo = fminf(lo, s_lo[i]); hi = fmaxf(hi, s_hi[i]); }
+                J.tickets[0] = 0u;
+                Params P;
+                P.error = __ldcg(&J.params->error);
+                if (any_bad) { P.error = TSNE_ERR_NONFINITE; lo = 0.0f; hi = 1.0f; }
+                float y_min, width;
+                int n_int;
+                if (J.force_box) {
+                    y_min = J.force_y_min;
+                    width = J.force_width;
+                    n_int = J.force_n_int;
+                } else {
+                    y_min = lo;
+                    width = __fsub_rn(hi, lo);
+                    if (!(width > 0.0f)) width = 1.0f;
+                    if (J.n_int_fixed > 0) {
+                        n_int = J.n_int_fixed;
+                    } else {
+                        float c = ceilf(width);
+                        if (c > (float)J.n_int_max) c = (float)J.n_int_max;
+                        n_int = (int)c;
+                        if (n_int < J.n_min) n_int = J.n_min;
+                        if (n_int > J.n_int_max) n_int = J.n_int_max;
+                        if (J.n_int_table) n_int = J.n_int_table[n_int];
+                    }
+                }
+                P.y_min = y_min;
+                P.width = width;
+                P.n_int = n_int;
+                P.b = __fdiv_rn(width, (float)n_int);
+                P.inv_b = __fdiv_rn(1.0f, P.b);
+                P.delta = __fdiv_rn(P.b, (float)p);
+                P.inv_delta = __fdiv_rn((float)p, P.b);
+                P.delta2 = __fmul_rn(P.delta, P.delta);
+                P.fx_shift = J.fx_shift;
+                P.fx_scale = ldexpf(1.0f, J.fx_shift);
+                P.fx_inv = ldexpf(1.0f, -J.fx_shift);
+                P.n = p * n_int;
+                P.n_boxes = (s == 2) ? n_int * n_int : n_int;
+                const int idx = tab.fft_of_n[P.n];
+                P.fft_idx = idx;
+                P.L = tab.fft[idx].L;
+                P.p_f = (float)p;
+                P.n_chunks = 0;
+                P.Z = 0.0;
+                P.inv_Z = 0.0f;
+                P.active = 1;
+                P.cur = cur;
+                P.pad = 0;
+                if (J.mode == kModeStep && !ignore_schedule) {
+                    const int it = J.dyn->iter;
+                    float a = 1.0f;
+                    if (it < J.early_iters) a = J.early_alpha;
+                    else if (J.late_iters > 0 && it >= J.n_iter - J.late_iters) a = J.late_alpha;
+                    P.alpha = a;
+                    P.momentum = it < J.mom_switch_iter ? J.momentum_early : J.momentum_late;
+                } else {
+                    P.alpha = J.alpha;
+                    P.momentum = 0.0f;
+                }
+                *J.params = P;
+                J.dyn->error = P.error;
+            }
+        }
+        __syncthreads();  // shared state of this item is consumed
     }
-    P.y_min = y_min;
-    P.width = width;
-    P.n_int = n_int;
-    P.b = __fdiv_rn(width, (float)n_int);
-    P.inv_b = __fdiv_rn(1.0f, P.b);
-    P.delta = __fdiv_rn(P.b, (float)p);
-    P.inv_delta = __fdiv_rn((float)p, P.b);
-    P.delta2 = __fmul_rn(P.delta, P.delta);
-    P.fx_shift = fx_shift;
-    P.fx_scale = ldexpf(1.0f, fx_shift);
-    P.fx_inv = ldexpf(1.0f, -fx_shift);
-    P.n = p * n_int;
-    P.n_boxes = (s == 2) ? n_int * n_int : n_int;
-    const int idx = fft_of_n[P.n];
-    P.fft_idx = idx;
-    P.L = table[idx].L;
-    P.p_f = (float)p;
-    P.pad = 0;
-    P.n_chunks = 0;
-    P.Z = 0.0;
-    P.inv_Z = 0.0f;
-    *params = P;
 }
 
 // ----------------------------------------------------------------------------
@@ -199,45 +255,56 @@ box_kernel(const float* __restrict__ Y, int64_t count, int s, int p, int n_int_f
 // scatter. Points of one box end up contiguous in sorted_y; their order
 // within the box is not fixed, which the integer spread sums do not see.
 // ----------------------------------------------------------------------------
-// Each block takes kSortPts consecutive points. With at most kHistBins
-// boxes the block first counts in a shared-memory histogram and touches the
-// global counters once per box it met, which keeps boxes holding many points
-// (tight clusters) from serialising on one global atomic; with more boxes
-// (each then holds few points) it uses the global counters directly.
+// Each work item takes kSortPts consecutive points of one job. With at most
+// kHistBins boxes the block first counts in a shared-memory histogram and
+// touches the global counters once per box it met, which keeps boxes holding
+// many points (tight clusters) from serialising on one global atomic; with
+// more boxes (each then holds few points) it uses the global counters
+// directly. The items of a job also zero its spread grids.
 template <int S>
 __global__ void __launch_bounds__(256)
-count_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ params,
-             int32_t* __restrict__ counts, long long* __restrict__ w) {
+count_kernel(const Job* __restrict__ jobs, int njobs) {
     extern __shared__ int32_t hist[];
-    const Params P = *params;
-    if (P.error) return;
-    const int nb = P.n_boxes;
-    {  // the spread grids of this iteration start at zero
-        const int64_t G = (S == 2) ? (int64_t)P.n * P.n : P.n;
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < (S + 1) * G; g += stride)
-            w[g] = 0;
-    }
-    const bool local = nb <= kHistBins;
+    __shared__ int32_t s_start[kMaxJobs + 1];
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return sort_items(J); });
     const int lane = threadIdx.x % 32;
-    if (local) {
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
-        __syncthreads();
-    }
-    const int64_t p0 = (int64_t)blockIdx.x * kSortPts;
-    for (int k = 0; k < kSortPts / 256; ++k) {
-        const int64_t i = p0 + k * 256 + threadIdx.x;
-        const int box = (i < N) ? box_of<S>(Y, i, P) : -1;
-        const unsigned peers = __match_any_sync(kFull, box);
-        if (box >= 0 && lane == __ffs(peers) - 1) {
-            if (local) atomicAdd(&hist[box], __popc(peers));
-            else atomicAdd(&counts[box], __popc(peers));
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = job_of(s_start, njobs, item);
+        const Job& J = jobs[j];
+        const int k = item - s_start[j], nk = s_start[j + 1] - s_start[j];
+        const Params P = *J.params;
+        const float* __restrict__ Y = J.ybuf[P.cur];
+        int32_t* __restrict__ counts = J.counts;
+        const int64_t N = J.N;
+        {  // the spread grids of this iteration start at zero
+            long long* __restrict__ w = J.w;
+            const int64_t G = (S == 2) ? (int64_t)P.n * P.n : P.n;
+            const int64_t stride = (int64_t)nk * blockDim.x;
+            for (int64_t g = (int64_t)k * blockDim.x + threadIdx.x; g < (S + 1) * G; g += stride)
+                w[g] = 0;
         }
-    }
-    if (local) {
+        const int nb = P.n_boxes;
+        const bool local = nb <= kHistBins;
+        if (local) {
+            for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+            __syncthreads();
+        }
+        const int64_t p0 = (int64_t)k * kSortPts;
+        for (int q = 0; q < kSortPts / 256; ++q) {
+            const int64_t i = p0 + q * 256 + threadIdx.x;
+            const int box = (i < N) ? box_of<S>(Y, i, P) : -1;
+            const unsigned peers = __match_any_sync(kFull, box);
+            if (box >= 0 && lane == __ffs(peers) - 1) {
+                if (local) atomicAdd(&hist[box], __popc(peers));
+                else atomicAdd(&counts[box], __popc(peers));
+            }
+        }
+        if (local) {
+            __syncthreads();
+            for (int b = threadIdx.x; b < nb; b += blockDim.x)
+                if (hist[b]) atomicAdd(&counts[b], hist[b]);
+        }
         __syncthreads();
-        for (int b = threadIdx.x; b < nb; b += blockDim.x)
-            if (hist[b]) atomicAdd(&counts[b], hist[b]);
     }
 }
 
@@ -246,51 +313,61 @@ count_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ 
 // plus its rank inside the block.
 template <int S>
 __global__ void __launch_bounds__(256)
-scatter_kernel(const float* __restrict__ Y, int64_t N, const Params* __restrict__ params,
-               int32_t* __restrict__ cursor, float* __restrict__ sorted_y) {
+scatter_kernel(const Job* __restrict__ jobs, int njobs) {
     extern __shared__ int32_t hist[];
+    __shared__ int32_t s_start[kMaxJobs + 1];
     constexpr int K = kSortPts / 256;
-    const Params P = *params;
-    if (P.error) return;
-    const int nb = P.n_boxes;
-    const bool local = nb <= kHistBins;
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return sort_items(J); });
     const int lane = threadIdx.x % 32;
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t p0 = (int64_t)blockIdx.x * kSortPts;
-    int box[K];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = job_of(s_start, njobs, item);
+        const Job& J = jobs[j];
+        const int k = item - s_start[j];
+        const Params P = *J.params;
+        const float* __restrict__ Y = J.ybuf[P.cur];
+        int32_t* __restrict__ cursor = J.cursor;
+        float* __restrict__ sorted_y = J.sorted_y;
+        const int64_t N = J.N;
+        const int nb = P.n_boxes;
+        const bool local = nb <= kHistBins;
+        const int64_t p0 = (int64_t)k * kSortPts;
+        int box[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int64_t i = p0 + k * 256 + threadIdx.x;
-        box[k] = (i < N) ? box_of<S>(Y, i, P) : -1;
-    }
-    if (local) {
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
-        __syncthreads();
+        for (int q = 0; q < K; ++q) {
+            const int64_t i = p0 + q * 256 + threadIdx.x;
+            box[q] = (i < N) ? box_of<S>(Y, i, P) : -1;
+        }
+        if (local) {
+            for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+            __syncthreads();
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const unsigned peers = __match_any_sync(kFull, box[k]);
-            if (box[k] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[box[k]], __popc(peers));
+            for (int q = 0; q < K; ++q) {
+                const unsigned peers = __match_any_sync(kFull, box[q]);
+                if (box[q] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[box[q]], __popc(peers));
+            }
+            __syncthreads();
+            for (int b = threadIdx.x; b < nb; b += blockDim.x)
+                if (hist[b]) hist[b] = atomicAdd(&cursor[b], hist[b]);
+            __syncthreads();
+        }
+        int32_t* dst_cursor = local ? hist : cursor;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const unsigned peers = __match_any_sync(kFull, box[q]);
+            const int leader = __ffs(peers) - 1;
+            int pos = 0;
+            if (box[q] >= 0 && lane == leader) pos = atomicAdd(&dst_cursor[box[q]], __popc(peers));
+            pos = __shfl_sync(kFull, pos, leader) + __popc(peers & lt);
+            if (box[q] >= 0) {
+                const int64_t i = p0 + q * 256 + threadIdx.x;
+                if (S == 2)
+                    reinterpret_cast<float2*>(sorted_y)[pos] = reinterpret_cast<const float2*>(Y)[i];
+                else
+                    sorted_y[pos] = Y[i];
+            }
         }
         __syncthreads();
-        for (int b = threadIdx.x; b < nb; b += blockDim.x)
-            if (hist[b]) hist[b] = atomicAdd(&cursor[b], hist[b]);
-        __syncthreads();
-    }
-    int32_t* dst_cursor = local ? hist : cursor;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const unsigned peers = __match_any_sync(kFull, box[k]);
-        const int leader = __ffs(peers) - 1;
-        int pos = 0;
-        if (box[k] >= 0 && lane == leader) pos = atomicAdd(&dst_cursor[box[k]], __popc(peers));
-        pos = __shfl_sync(kFull, pos, leader) + __popc(peers & lt);
-        if (box[k] >= 0) {
-            const int64_t i = p0 + k * 256 + threadIdx.x;
-            if (S == 2)
-                reinterpret_cast<float2*>(sorted_y)[pos] = reinterpret_cast<const float2*>(Y)[i];
-            else
-                sorted_y[pos] = Y[i];
-        }
     }
 }
 
@@ -321,106 +398,123 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* smem_warp, int& 
     return excl;
 }
 
-// Pass 1: per-block totals of points and of spread chunks (ceil(count/kChunk));
-// the last block turns them into exclusive block offsets.
+// Pass 1: per-item totals of points and of spread chunks (ceil(count/chunk));
+// the last item of a job turns them into exclusive offsets.
 __global__ void __launch_bounds__(1024)
-scan_blocks_kernel(const int32_t* __restrict__ counts, Params* params,
-                   int32_t* __restrict__ block_pts, int32_t* __restrict__ block_chunks,
-                   unsigned* __restrict__ ticket) {
+scan_blocks_kernel(const Job* __restrict__ jobs, int njobs) {
+    __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ int sw[32];
     __shared__ bool s_last;
-    const int nb = params->n_boxes;
-    const int base = blockIdx.x * kScanBlock + threadIdx.x * 2;
-    int c0 = base < nb ? counts[base] : 0;
-    int c1 = base + 1 < nb ? counts[base + 1] : 0;
-    int pts = c0 + c1;
-    int chk = (c0 + kChunk - 1) / kChunk + (c1 + kChunk - 1) / kChunk;
-    int tp, tc;
-    block_exclusive_scan(pts, sw, tp);
-    block_exclusive_scan(chk, sw, tc);
-    if (threadIdx.x == 0) {
-        block_pts[blockIdx.x] = tp;
-        block_chunks[blockIdx.x] = tc;
-        __threadfence();
-        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    int carry_p = 0, carry_c = 0;
-    for (unsigned start = 0; start < gridDim.x; start += blockDim.x) {
-        const unsigned i = start + threadIdx.x;
-        int vp = i < gridDim.x ? __ldcg(&block_pts[i]) : 0;
-        int vc = i < gridDim.x ? __ldcg(&block_chunks[i]) : 0;
-        int sp, sc;
-        int ep = block_exclusive_scan(vp, sw, sp);
-        int ec = block_exclusive_scan(vc, sw, sc);
-        if (i < gridDim.x) {
-            block_pts[i] = carry_p + ep;
-            block_chunks[i] = carry_c + ec;
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return scan_items(J); });
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = job_of(s_start, njobs, item);
+        const Job& J = jobs[j];
+        const int k = item - s_start[j], nk = s_start[j + 1] - s_start[j];
+        const int nb = J.params->n_boxes;
+        const int ch = J.chunk;
+        const int32_t* __restrict__ counts = J.counts;
+        const int base = k * kScanBlock + threadIdx.x * 2;
+        const int c0 = base < nb ? counts[base] : 0;
+        const int c1 = base + 1 < nb ? counts[base + 1] : 0;
+        const int pts = c0 + c1;
+        const int chk = (c0 + ch - 1) / ch + (c1 + ch - 1) / ch;
+        int tp, tc;
+        block_exclusive_scan(pts, sw, tp);
+        block_exclusive_scan(chk, sw, tc);
+        if (threadIdx.x == 0) {
+            J.block_pts[k] = tp;
+            J.block_chunks[k] = tc;
+            __threadfence();
+            s_last = (atomicAdd(&J.tickets[1], 1u) == (unsigned)nk - 1);
         }
-        carry_p += sp;
-        carry_c += sc;
-    }
-    if (threadIdx.x == 0) {
-        params->n_chunks = carry_c;
-        *ticket = 0u;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            int carry_p = 0, carry_c = 0;
+            for (int start = 0; start < nk; start += blockDim.x) {
+                const int i = start + threadIdx.x;
+                const int vp = i < nk ? __ldcg(&J.block_pts[i]) : 0;
+                const int vc = i < nk ? __ldcg(&J.block_chunks[i]) : 0;
+                int sp, sc;
+                const int ep = block_exclusive_scan(vp, sw, sp);
+                const int ec = block_exclusive_scan(vc, sw, sc);
+                if (i < nk) {
+                    J.block_pts[i] = carry_p + ep;
+                    J.block_chunks[i] = carry_c + ec;
+                }
+                carry_p += sp;
+                carry_c += sc;
+            }
+            if (threadIdx.x == 0) {
+                J.params->n_chunks = carry_c;
+                J.tickets[1] = 0u;
+            }
+        }
+        __syncthreads();
     }
 }
 
 // Pass 2: box offsets, scatter cursors, chunk -> box table; resets the counts
 // for the next iteration. Each warp writes the chunk entries of its 64 boxes
 // with its lanes in parallel (a box holding many points has many chunks).
-template <int S, int PP>
 __global__ void __launch_bounds__(1024)
-scan_boxes_kernel(int32_t* __restrict__ counts, const Params* __restrict__ params,
-                  const int32_t* __restrict__ block_pts, const int32_t* __restrict__ block_chunks,
-                  int32_t* __restrict__ box_start, int32_t* __restrict__ cursor,
-                  int32_t* __restrict__ chunk_start, int32_t* __restrict__ chunk_box, int64_t N) {
+scan_boxes_kernel(const Job* __restrict__ jobs, int njobs) {
+    __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ int sw[32];
-    const Params P = *params;
-    const int nb = P.n_boxes;
-    if (blockIdx.x * kScanBlock >= nb) return;  // uniform per block
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return scan_items(J); });
     const int lane = threadIdx.x % 32;
-    const int base = blockIdx.x * kScanBlock + threadIdx.x * 2;
-    int c[2] = {base < nb ? counts[base] : 0, base + 1 < nb ? counts[base + 1] : 0};
-    int k[2] = {(c[0] + kChunk - 1) / kChunk, (c[1] + kChunk - 1) / kChunk};
-    int tp, tc;
-    int ep = block_exclusive_scan(c[0] + c[1], sw, tp) + block_pts[blockIdx.x];
-    int ec = block_exclusive_scan(k[0] + k[1], sw, tc) + block_chunks[blockIdx.x];
-    int ecb[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int b = base + u;
-        ecb[u] = ec;
-        if (b < nb) {
-            box_start[b] = ep;
-            cursor[b] = ep;
-            chunk_start[b] = ec;
-            counts[b] = 0;
-            if (b == nb - 1) {
-                box_start[nb] = (int32_t)N;
-                chunk_start[nb] = ec + k[u];
-            }
-        }
-        ep += c[u];
-        ec += k[u];
-    }
-    // chunk -> box entries: the warp visits its lanes' boxes one by one
-    for (int src = 0; src < 32; ++src) {
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = job_of(s_start, njobs, item);
+        const Job& J = jobs[j];
+        const int k = item - s_start[j];
+        const int nb = J.params->n_boxes;
+        const int ch = J.chunk;
+        int32_t* __restrict__ counts = J.counts;
+        int32_t* __restrict__ box_start = J.box_start;
+        int32_t* __restrict__ cursor = J.cursor;
+        int32_t* __restrict__ chunk_start = J.chunk_start;
+        int32_t* __restrict__ chunk_box = J.chunk_box;
+        const int base = k * kScanBlock + threadIdx.x * 2;
+        int c[2] = {base < nb ? counts[base] : 0, base + 1 < nb ? counts[base + 1] : 0};
+        int kk[2] = {(c[0] + ch - 1) / ch, (c[1] + ch - 1) / ch};
+        int tp, tc;
+        int ep = block_exclusive_scan(c[0] + c[1], sw, tp) + J.block_pts[k];
+        int ec = block_exclusive_scan(kk[0] + kk[1], sw, tc) + J.block_chunks[k];
+        int ecb[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int b = __shfl_sync(kFull, base + u, src);
-            const int kb = __shfl_sync(kFull, k[u], src);
-            const int eb = __shfl_sync(kFull, ecb[u], src);
-            if (b < nb)
-                for (int q = lane; q < kb; q += 32) chunk_box[eb + q] = b;
+            const int b = base + u;
+            ecb[u] = ec;
+            if (b < nb) {
+                box_start[b] = ep;
+                cursor[b] = ep;
+                chunk_start[b] = ec;
+                counts[b] = 0;
+                if (b == nb - 1) {
+                    box_start[nb] = (int32_t)J.N;
+                    chunk_start[nb] = ec + kk[u];
+                }
+            }
+            ep += c[u];
+            ec += kk[u];
         }
+        // chunk -> box entries: the warp visits its lanes' boxes one by one
+        for (int src = 0; src < 32; ++src) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int b = __shfl_sync(kFull, base + u, src);
+                const int kb = __shfl_sync(kFull, kk[u], src);
+                const int eb = __shfl_sync(kFull, ecb[u], src);
+                if (b < nb)
+                    for (int q = lane; q < kb; q += 32) chunk_box[eb + q] = b;
+            }
+        }
+        __syncthreads();
     }
 }
 
 // ----------------------------------------------------------------------------
-// Step 1 (spread): one warp per chunk of at most kChunk points of one box.
+// Step 1 (spread): one warp per chunk of at most J.chunk points of one box.
 // For node g = (j1, j2) of the box and a point with local coordinates t
 // (units of delta), the point adds W = L_j1(t1) L_j2(t2) to the charge grid
 // w0 and W (t_m - j_m - 1/2) to the dipole grids d_m, the charge y(m) taken
@@ -435,26 +529,34 @@ scan_boxes_kernel(int32_t* __restrict__ counts, const Params* __restrict__ param
 // ----------------------------------------------------------------------------
 template <int S, int PP>
 __global__ void __launch_bounds__(256)
-spread_kernel(const float* __restrict__ sorted_y, const int32_t* __restrict__ box_start,
-              const int32_t* __restrict__ chunk_start, const int32_t* __restrict__ chunk_box,
-              const Params* __restrict__ params, long long* __restrict__ w) {
+spread_kernel(const Job* __restrict__ jobs, int njobs) {
     constexpr int NODES = (S == 2) ? PP * PP : PP;
     constexpr int NVAL = (S + 1) * NODES;
     constexpr int NV = (NVAL + 31) / 32 * 32;
-    const Params P = *params;
-    if (P.error) return;
+    __shared__ int32_t s_start[kMaxJobs + 1];
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) {
+        const Params* P = J.params;
+        return job_live(*P) ? P->n_chunks : 0;
+    });
     const int lane = threadIdx.x % 32;
     const int nwarp = gridDim.x * blockDim.x / 32;
-    const int n = P.n;
-    const int64_t G = (S == 2) ? (int64_t)n * n : n;
-    const float sc = P.fx_scale;
-    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) / 32; q < P.n_chunks; q += nwarp) {
-        const int box = chunk_box[q];
-        const int bs = box_start[box];
-        const int cnt = box_start[box + 1] - bs;
-        const int ci = q - chunk_start[box];
-        const int start = bs + ci * kChunk;
-        const int len = min(kChunk, cnt - ci * kChunk);
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) / 32; q < total; q += nwarp) {
+        const int jb = job_of(s_start, njobs, q);
+        const Job& J = jobs[jb];
+        const Params P = *J.params;
+        const int ql = q - s_start[jb];
+        const int chunk = J.chunk;
+        const float* __restrict__ sorted_y = J.sorted_y;
+        long long* __restrict__ w = J.w;
+        const int n = P.n;
+        const int64_t G = (S == 2) ? (int64_t)n * n : n;
+        const float sc = P.fx_scale;
+        const int box = J.chunk_box[ql];
+        const int bs = J.box_start[box];
+        const int cnt = J.box_start[box + 1] - bs;
+        const int ci = ql - J.chunk_start[box];
+        const int start = bs + ci * chunk;
+        const int len = min(chunk, cnt - ci * chunk);
         const int bx = (S == 2) ? box / P.n_int : box;
         const int by = (S == 2) ? box % P.n_int : 0;
         long long acc[NV];
@@ -468,15 +570,15 @@ spread_kernel(const float* __restrict__ sorted_y, const int32_t* __restrict__ bo
                 lagrange<PP>(t1, L1);
                 lagrange<PP>(t2, L2);
 #pragma unroll
-                for (int j = 0; j < PP; ++j) {
-                    e1[j] = t1 - ((float)j + 0.5f);
-                    e2[j] = t2 - ((float)j + 0.5f);
+                for (int jj = 0; jj < PP; ++jj) {
+                    e1[jj] = t1 - ((float)jj + 0.5f);
+                    e2[jj] = t2 - ((float)jj + 0.5f);
                 }
             } else {
                 const float t1 = local_t(sorted_y[start + k], bx, P);
                 lagrange<PP>(t1, L1);
 #pragma unroll
-                for (int j = 0; j < PP; ++j) e1[j] = t1 - ((float)j + 0.5f);
+                for (int jj = 0; jj < PP; ++jj) e1[jj] = t1 - ((float)jj + 0.5f);
             }
 #pragma unroll
             for (int j1 = 0; j1 < PP; ++j1) {
@@ -491,17 +593,17 @@ spread_kernel(const float* __restrict__ sorted_y, const int32_t* __restrict__ bo
             }
         }
         warp_transpose_reduce<NV>(acc, lane);
-        const bool multi = cnt > kChunk;
+        const bool multi = cnt > chunk;
 #pragma unroll
         for (int g = 0; g < NV / 32; ++g) {
             const int v = g * 32 + lane;
             if (v < NVAL) {
-                const int ch = v / NODES, node = v % NODES;
+                const int chn = v / NODES, node = v % NODES;
                 const int j1 = (S == 2) ? node / PP : node;
                 const int j2 = (S == 2) ? node % PP : 0;
                 const int64_t gi = (S == 2) ? (int64_t)(bx * PP + j1) * n + (by * PP + j2)
                                             : (int64_t)(bx * PP + j1);
-                long long* dst = &w[ch * G + gi];
+                long long* dst = &w[chn * G + gi];
                 if (multi)
                     atomicAdd(reinterpret_cast<unsigned long long*>(dst),
                               static_cast<unsigned long long>(acc[g * 32]));
@@ -543,35 +645,17 @@ __device__ __forceinline__ float update_one(float y, float dy, float& u, float& 
     return y + u;
 }
 
-#ifndef FITSNE_GATHER_L2_ONLY
-#define FITSNE_GATHER_L2_ONLY 0  // 1: the Y[j] gathers bypass L1 (ld.global.cg)
-#endif
-
-// y_j from the shared-memory window [w0, w0 + wn) of a relabelled run when it
-// holds j, else from global memory.
-struct Window {
-    const float* s;  // shared copy of Y[w0 .. w0 + wn)
-    int w0, wn;
-};
-
-template <int S, bool WIN>
+template <int S>
 __device__ __forceinline__ void attract(float yi0, float yi1, int j, float v,
-                                        const float* __restrict__ Y, const Window& win,
-                                        float& a0, float& a1) {
-    const unsigned off = (unsigned)(j - win.w0);
-    const bool in = WIN && off < (unsigned)win.wn;
+                                        const float* __restrict__ Y, float& a0, float& a1) {
     if (S == 2) {
-        float2 yj;
-        if (in) yj = reinterpret_cast<const float2*>(win.s)[off];
-        else yj = FITSNE_GATHER_L2_ONLY ? __ldcg(reinterpret_cast<const float2*>(Y) + j)
-                                        : __ldg(reinterpret_cast<const float2*>(Y) + j);
+        const float2 yj = __ldg(reinterpret_cast<const float2*>(Y) + j);
         const float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
         const float q = __fdividef(v, 1.0f + d0 * d0 + d1 * d1);
         a0 += q * d0;
         a1 += q * d1;
     } else {
-        const float yj = in ? win.s[off] : (FITSNE_GATHER_L2_ONLY ? __ldcg(Y + j) : __ldg(Y + j));
-        const float d0 = yi0 - yj;
+        const float d0 = yi0 - __ldg(Y + j);
         a0 += __fdividef(v, 1.0f + d0 * d0) * d0;
     }
 }
@@ -590,29 +674,26 @@ __device__ __forceinline__ void load_slots(const int32_t* __restrict__ col,
 
 // Attraction of one row from its prefetched entries (and any beyond 32 U),
 // summed over the warp.
-template <int S, bool WIN, int U>
+template <int S, int U>
 __device__ __forceinline__ void attract_row(const int32_t* __restrict__ col,
                                             const float* __restrict__ val,
-                                            const float* __restrict__ Y, const Window& win,
-                                            int beg, int end, float yi0, float yi1, int lane,
-                                            const int (&jj)[U], const float (&vv)[U], float& a0,
-                                            float& a1) {
+                                            const float* __restrict__ Y, int beg, int end,
+                                            float yi0, float yi1, int lane, const int (&jj)[U],
+                                            const float (&vv)[U], float& a0, float& a1) {
     a0 = 0.0f;
     a1 = 0.0f;
 #pragma unroll
     for (int u = 0; u < U; ++u)
-        if (beg + lane + 32 * u < end) attract<S, WIN>(yi0, yi1, jj[u], vv[u], Y, win, a0, a1);
+        if (beg + lane + 32 * u < end) attract<S>(yi0, yi1, jj[u], vv[u], Y, a0, a1);
     for (int e = beg + lane + 32 * U; e < end; e += 32)
-        attract<S, WIN>(yi0, yi1, __ldcs(&col[e]), __ldcs(&val[e]), Y, win, a0, a1);
+        attract<S>(yi0, yi1, __ldcs(&col[e]), __ldcs(&val[e]), Y, a0, a1);
     a0 = warp_sum(a0);
     if (S == 2) a1 = warp_sum(a1);
 }
 
-// A CTA takes chunks of kForceChunk = 256 consecutive points (rows of P);
-// warp w of the CTA owns rows 32 w .. 32 w + 31 of the chunk. In a relabelled
-// run (WIN) the CTA first copies the window of Y centred on the chunk's mean
-// neighbour label into shared memory, and the attraction reads y_j there
-// when the window holds j. Per 32-row block:
+// A work item is a chunk of kForceChunk = 256 consecutive points (rows of P)
+// of one job; warp w of the CTA owns rows 32 w .. 32 w + 31 of the chunk.
+// Per 32-row block:
 //  1. lane l takes point i0 + l: its row bounds, coordinates, optimizer state
 //     (coalesced), its box, local coordinates and Lagrange weights, and the
 //     Step 3 interpolation of the node values of its box -> F_rep;
@@ -627,54 +708,35 @@ __device__ __forceinline__ void attract_row(const int32_t* __restrict__ col,
 #define FITSNE_FORCE_MINB 4   // resident 256-thread blocks per SM the registers must allow
 #endif
 
-template <int S, int PP, bool STEP, bool WIN>
-__global__ void __launch_bounds__(256, WIN ? 2 : FITSNE_FORCE_MINB)
-force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-             const float* __restrict__ val, const float* __restrict__ Y,
-             const Params* __restrict__ params, const float4* __restrict__ hgrid, float alpha,
-             float* __restrict__ dY, StepArgs sa, int64_t N,
-             const int32_t* __restrict__ chunk_centre, int win_cap) {
+template <int S, int PP, bool STEP>
+__global__ void __launch_bounds__(256, FITSNE_FORCE_MINB)
+force_kernel(const Job* __restrict__ jobs, int njobs) {
     constexpr int U = FITSNE_FORCE_SLOTS;
-    extern __shared__ float s_win[];
-    const Params P = *params;
-    if (P.error) return;
+    __shared__ int32_t s_start[kMaxJobs + 1];
+    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) {
+        const Params* P = J.params;
+        return job_live(*P) ? (int)((J.N + kForceChunk - 1) / kForceChunk) : 0;
+    });
     const int lane = threadIdx.x % 32;
-    const float fs = P.delta * P.inv_Z;
-    const int n = P.n;
-    Window win{s_win, 0, 0};
-#ifndef FITSNE_FORCE_CONTIG
-#define FITSNE_FORCE_CONTIG 0  // 1: each CTA takes a contiguous range of chunks
-#endif
-    const int64_t nch = (N + kForceChunk - 1) / kForceChunk;
-    const int64_t c_lo = FITSNE_FORCE_CONTIG ? nch * blockIdx.x / gridDim.x : blockIdx.x;
-    const int64_t c_hi = FITSNE_FORCE_CONTIG ? nch * (blockIdx.x + 1) / gridDim.x : nch;
-    const int64_t c_step = FITSNE_FORCE_CONTIG ? 1 : gridDim.x;
-    for (int64_t c = c_lo; c < c_hi; c += c_step) {
-        if (WIN) {
-            __syncthreads();  // the previous chunk's readers are done
-            const int64_t wn = N < win_cap ? N : win_cap;
-            int64_t w0 = (int64_t)chunk_centre[c] - wn / 2;
-            if (w0 > N - wn) w0 = N - wn;
-            if (w0 < 0) w0 = 0;
-            w0 &= ~(int64_t)3;  // 16-byte aligned staging loads
-            win.w0 = (int)w0;
-            win.wn = (int)wn;
-            for (int t = threadIdx.x; t < wn * S / 4; t += blockDim.x)
-                reinterpret_cast<float4*>(s_win)[t] = __ldg(reinterpret_cast<const float4*>(Y + w0 * S) + t);
-            for (int t = (int)(wn * S / 4) * 4 + threadIdx.x; t < wn * S; t += blockDim.x)
-                s_win[t] = __ldg(Y + w0 * S + t);
-            __syncthreads();
-        }
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int jb = job_of(s_start, njobs, item);
+        const Job& J = jobs[jb];
+        const int64_t c = item - s_start[jb];
+        const int64_t N = J.N;
         const int64_t i0 = c * kForceChunk + (threadIdx.x / 32) * 32;
         if (i0 >= N) continue;
+        const Params* __restrict__ Pp = J.params;
+        const int32_t* __restrict__ col = J.col;
+        const float* __restrict__ val = J.val;
+        const float* __restrict__ Y = J.ybuf[Pp->cur];
         const int64_t i = i0 + lane;
         const bool live = i < N;
         const int nrows = (N - i0) < 32 ? (int)(N - i0) : 32;
         // 1. per-point work, one point per lane
         int rp_lo = 0, rp_hi = 0;
         float yi0 = 0.0f, yi1 = 0.0f, f0 = 0.0f, f1 = 0.0f;
-        float2 us = make_float2(0.0f, 0.0f), gs = make_float2(0.0f, 0.0f);
         if (live) {
+            const int32_t* __restrict__ row_ptr = J.row_ptr;
             rp_lo = __ldg(&row_ptr[i]);
             rp_hi = __ldg(&row_ptr[i + 1]);
             if (S == 2) {
@@ -684,16 +746,10 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             } else {
                 yi0 = Y[i];
             }
-            if (STEP) {
-                if (S == 2) {
-                    us = reinterpret_cast<const float2*>(sa.uY)[i];
-                    gs = reinterpret_cast<const float2*>(sa.gains)[i];
-                } else {
-                    us.x = sa.uY[i];
-                    gs.x = sa.gains[i];
-                }
-            }
             // Step 3: (h_{m+1} - y(m) h_{s+2})(y_i) = delta sum_g L_g [u'_m + (j_m + 1/2 - t_m) v]
+            const Params& P = *Pp;
+            const float4* __restrict__ hgrid = J.hgrid;
+            const int n = P.n;
             const int l1 = interval_of(yi0, P);
             const float t1 = local_t(yi0, l1, P);
             float L1[PP];
@@ -740,7 +796,7 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             {
                 const float y0 = __shfl_sync(kFull, yi0, r), y1 = __shfl_sync(kFull, yi1, r);
                 float a0, a1;
-                attract_row<S, WIN, U>(col, val, Y, win, bA, eA, y0, y1, lane, jA, vA, a0, a1);
+                attract_row<S, U>(col, val, Y, bA, eA, y0, y1, lane, jA, vA, a0, a1);
                 if (lane == r) { A0 = a0; A1 = a1; }
             }
             if (hasB) {
@@ -750,18 +806,33 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
                 }
                 const float y0 = __shfl_sync(kFull, yi0, r + 1), y1 = __shfl_sync(kFull, yi1, r + 1);
                 float a0, a1;
-                attract_row<S, WIN, U>(col, val, Y, win, bB, eB, y0, y1, lane, jB, vB, a0, a1);
+                attract_row<S, U>(col, val, Y, bB, eB, y0, y1, lane, jB, vB, a0, a1);
                 if (lane == r + 1) { A0 = a0; A1 = a1; }
             }
         }
-        // 3. gradient (and update) of this lane's point
+        // 3. gradient (and update) of this lane's point; the job's output
+        //    pointers and schedule values are read only now
         if (live) {
+            const Params& P = *Pp;
+            const float fs = P.delta * P.inv_Z;
+            const float alpha = P.alpha;
             const float g0 = 4.0f * (alpha * A0 + f0 * fs);
             const float g1 = (S == 2) ? 4.0f * (alpha * A1 + f1 * fs) : 0.0f;
             if (!STEP) {
+                float* __restrict__ dY = J.dY;
                 if (S == 2) reinterpret_cast<float2*>(dY)[i] = make_float2(g0, g1);
                 else dY[i] = g0;
             } else {
+                const StepArgs sa{J.ybuf[P.cur ^ 1], J.uY, J.gains, P.momentum, J.lr, J.min_gain,
+                                  J.gain_inc, J.gain_dec};
+                float2 us, gs;
+                if (S == 2) {
+                    us = reinterpret_cast<const float2*>(sa.uY)[i];
+                    gs = reinterpret_cast<const float2*>(sa.gains)[i];
+                } else {
+                    us = make_float2(sa.uY[i], 0.0f);
+                    gs = make_float2(sa.gains[i], 0.0f);
+                }
                 const float n0 = update_one(yi0, g0, us.x, gs.x, sa);
                 if (S == 2) {
                     const float n1 = update_one(yi1, g1, us.y, gs.y, sa);
@@ -776,6 +847,19 @@ force_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             }
         }
     }
+}
+
+// Moves every stepping job that took part in this iteration to the next one:
+// the new Y becomes current and the schedule index advances.
+__global__ void advance_kernel(const Job* __restrict__ jobs, int njobs) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= njobs) return;
+    const Job& J = jobs[j];
+    if (J.mode != kModeStep) return;
+    if (!J.params->active) return;
+    JobDyn* d = J.dyn;
+    d->cur ^= 1;
+    d->iter += 1;
 }
 
 // ----------------------------------------------------------------------------
@@ -873,126 +957,98 @@ __global__ void fill_kernel(float* __restrict__ a, float v, int64_t n) {
 }
 
 // ----------------------------------------------------------------------------
-// Launchers
+// Launchers. Grids are sized from the table's capacities (TableCaps) only.
 // ----------------------------------------------------------------------------
-static int grid_for(const tsne_plan* pl, int64_t items, int per_block, int per_sm) {
+static int grid_cap(int64_t items, int per_block, int64_t cap) {
     int64_t b = (items + per_block - 1) / per_block;
-    int64_t cap = (int64_t)pl->sm_count * per_sm;
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
 }
 
-cudaError_t launch_box(tsne_plan* pl, const float* Y) {
-    box_kernel<<<kBoxBlocks, kBoxThreads, 0, pl->stream>>>(
-        Y, pl->N * pl->s, pl->s, pl->p, pl->n_int_fixed, pl->n_min, pl->n_int_max, pl->force_box,
-        pl->force_y_min, pl->force_width, pl->force_n_int, pl->fx_shift, pl->box_partial,
-        pl->tickets + 0,
-        pl->params, pl->fft_table, pl->fft_of_n);
-    pl->launches += 1;
+cudaError_t launch_box(const Job* jobs, const TableCaps& c, const Tables& t, int ignore_schedule,
+                       cudaStream_t st) {
+    const int g = grid_cap(c.sum_box_items, 1, 4LL * c.sm_count);
+    box_kernel<<<g, kBoxThreads, 0, st>>>(jobs, c.njobs, c.s, c.p, ignore_schedule, t);
     return cudaGetLastError();
 }
 
 template <int S, int PP>
-static void sort_and_spread_impl(tsne_plan* pl, const float* Y) {
-    const int gp = (int)((pl->N + kSortPts - 1) / kSortPts);
+static void sort_and_spread_impl(const Job* jobs, const TableCaps& c, cudaStream_t st) {
+    const int gp = grid_cap(c.sum_N, kSortPts, 8LL * c.sm_count);
     const size_t hs = sizeof(int32_t) * kHistBins;
-    count_kernel<S><<<gp, 256, hs, pl->stream>>>(Y, pl->N, pl->params, pl->counts, pl->w);
-    scan_blocks_kernel<<<pl->scan_blocks, 1024, 0, pl->stream>>>(
-        pl->counts, pl->params, pl->block_pts, pl->block_chunks, pl->tickets + 1);
-    scan_boxes_kernel<S, PP><<<pl->scan_blocks, 1024, 0, pl->stream>>>(
-        pl->counts, pl->params, pl->block_pts, pl->block_chunks, pl->box_start, pl->cursor,
-        pl->chunk_start, pl->chunk_box, pl->N);
-    scatter_kernel<S><<<gp, 256, hs, pl->stream>>>(Y, pl->N, pl->params, pl->cursor, pl->sorted_y);
-    const int gs = grid_for(pl, pl->chunk_cap * 32, 256, 8);
-    spread_kernel<S, PP><<<gs, 256, 0, pl->stream>>>(pl->sorted_y, pl->box_start, pl->chunk_start,
-                                                     pl->chunk_box, pl->params, pl->w);
-    pl->launches += 5;
+    count_kernel<S><<<gp, 256, hs, st>>>(jobs, c.njobs);
+    const int gsc = grid_cap((int64_t)c.njobs * c.max_scan_items, 1, 2LL * c.sm_count);
+    scan_blocks_kernel<<<gsc, 1024, 0, st>>>(jobs, c.njobs);
+    scan_boxes_kernel<<<gsc, 1024, 0, st>>>(jobs, c.njobs);
+    scatter_kernel<S><<<gp, 256, hs, st>>>(jobs, c.njobs);
+    const int gs = grid_cap(c.sum_chunk_cap * 32, 256, 8LL * c.sm_count);
+    spread_kernel<S, PP><<<gs, 256, 0, st>>>(jobs, c.njobs);
 }
 
 #define FITSNE_DISPATCH(S_, FN, ...)                                   \
-    switch (pl->p) {                                                   \
+    switch (c.p) {                                                     \
         case 2: FN<S_, 2>(__VA_ARGS__); break;                         \
         case 3: FN<S_, 3>(__VA_ARGS__); break;                         \
         case 4: FN<S_, 4>(__VA_ARGS__); break;                         \
         default: FN<S_, 5>(__VA_ARGS__); break;                        \
     }
 
-cudaError_t launch_sort_and_spread(tsne_plan* pl, const float* Y) {
-    if (pl->s == 2) { FITSNE_DISPATCH(2, sort_and_spread_impl, pl, Y); }
-    else { FITSNE_DISPATCH(1, sort_and_spread_impl, pl, Y); }
+cudaError_t launch_sort_and_spread(const Job* jobs, const TableCaps& c, cudaStream_t st) {
+    if (c.s == 2) { FITSNE_DISPATCH(2, sort_and_spread_impl, jobs, c, st); }
+    else { FITSNE_DISPATCH(1, sort_and_spread_impl, jobs, c, st); }
     return cudaGetLastError();
 }
 
-template <int S, int PP, bool STEP, bool WIN>
-static void force_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha, float* dY,
-                       StepArgs sa) {
-    if (WIN) {
-        const int64_t nch = (pl->N + kForceChunk - 1) / kForceChunk;
-        const int ctas = (int)std::min<int64_t>(nch, 2LL * pl->sm_count);
-        const int cap = FITSNE_WIN_BYTES / (int)(sizeof(float) * S);
-        force_kernel<S, PP, STEP, true><<<ctas, 256, FITSNE_WIN_BYTES, pl->stream>>>(
-            P.row_ptr, P.col, P.val, Y, pl->params, pl->hgrid, alpha, dY, sa, pl->N,
-            pl->chunk_centre, cap);
-    } else {
-        const int g = grid_for(pl, pl->N, 256, 8);
-        force_kernel<S, PP, STEP, false><<<g, 256, 0, pl->stream>>>(
-            P.row_ptr, P.col, P.val, Y, pl->params, pl->hgrid, alpha, dY, sa, pl->N, nullptr, 0);
-    }
-    pl->launches += 1;
-}
-
 template <int S, int PP>
-static void gradient_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,
-                          float* dY) {
-    force_impl<S, PP, false, false>(pl, P, Y, alpha, dY, StepArgs{});
+static void forces_impl(const Job* jobs, const TableCaps& c, int step, cudaStream_t st) {
+    const int g = grid_cap(c.sum_N, kForceChunk, 8LL * c.sm_count);
+    if (step) force_kernel<S, PP, true><<<g, 256, 0, st>>>(jobs, c.njobs);
+    else force_kernel<S, PP, false><<<g, 256, 0, st>>>(jobs, c.njobs);
 }
 
-#ifndef FITSNE_RELABEL_WINDOW
-#define FITSNE_RELABEL_WINDOW 0  // 1: relabelled runs read y_j through a shared-memory window
-#endif
-
-template <int S, int PP>
-static void step_impl(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,
-                      const StepArgs& sa) {
-    if (pl->reordered && FITSNE_RELABEL_WINDOW) force_impl<S, PP, true, true>(pl, P, Y, alpha, nullptr, sa);
-    else force_impl<S, PP, true, false>(pl, P, Y, alpha, nullptr, sa);
-}
-
-template <int S, int PP>
-static cudaError_t configure_impl() {
-    return cudaFuncSetAttribute(force_kernel<S, PP, true, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, FITSNE_WIN_BYTES);
-}
-
-cudaError_t force_configure(tsne_plan* pl) {
-    cudaError_t e = cudaSuccess;
-    switch (pl->p * 10 + pl->s) {
-        case 21: e = configure_impl<1, 2>(); break;
-        case 22: e = configure_impl<2, 2>(); break;
-        case 31: e = configure_impl<1, 3>(); break;
-        case 32: e = configure_impl<2, 3>(); break;
-        case 41: e = configure_impl<1, 4>(); break;
-        case 42: e = configure_impl<2, 4>(); break;
-        case 51: e = configure_impl<1, 5>(); break;
-        default: e = configure_impl<2, 5>(); break;
-    }
-    return e;
-}
-
-cudaError_t launch_gradient(tsne_plan* pl, const tsne_csr& P, const float* Y, float alpha,
-                            float* dY) {
-    if (pl->s == 2) { FITSNE_DISPATCH(2, gradient_impl, pl, P, Y, alpha, dY); }
-    else { FITSNE_DISPATCH(1, gradient_impl, pl, P, Y, alpha, dY); }
+cudaError_t launch_forces(const Job* jobs, const TableCaps& c, int step, cudaStream_t st) {
+    if (c.s == 2) { FITSNE_DISPATCH(2, forces_impl, jobs, c, step, st); }
+    else { FITSNE_DISPATCH(1, forces_impl, jobs, c, step, st); }
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(tsne_plan* pl, const tsne_csr& P, const float* Y, float* Y_new,
-                        float* uY, float* gains, float alpha, float momentum, float lr,
-                        float min_gain, float gain_inc, float gain_dec) {
-    StepArgs sa{Y_new, uY, gains, momentum, lr, min_gain, gain_inc, gain_dec};
-    if (pl->s == 2) { FITSNE_DISPATCH(2, step_impl, pl, P, Y, alpha, sa); }
-    else { FITSNE_DISPATCH(1, step_impl, pl, P, Y, alpha, sa); }
+cudaError_t launch_advance(const Job* jobs, int njobs, cudaStream_t st) {
+    advance_kernel<<<(njobs + 255) / 256, 256, 0, st>>>(jobs, njobs);
+    return cudaGetLastError();
+}
+
+int phase_launches(int s) { return 1 + 5 + (s == 2 ? 3 : 1) + 1; }
+
+__global__ void job_write_kernel(Job* __restrict__ dst, Job job, JobDyn* __restrict__ dyn_dst,
+                                 JobDyn dyn, int with_dyn) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *dst = job;
+        if (with_dyn) *dyn_dst = dyn;
+    }
+}
+
+__global__ void copy_current_kernel(const Job* __restrict__ row, int64_t count,
+                                    float* __restrict__ dst) {
+    const float* __restrict__ src = row->ybuf[row->dyn->cur];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        dst[i] = src[i];
+}
+
+cudaError_t launch_copy_current(const Job* row, int64_t count, float* dst, cudaStream_t st) {
+    int64_t b = (count + 255) / 256;
+    if (b > 1024) b = 1024;
+    if (b < 1) b = 1;
+    copy_current_kernel<<<(int)b, 256, 0, st>>>(row, count, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_job_write(Job* dst, const Job& job, JobDyn* dyn_dst, const JobDyn* dyn,
+                             cudaStream_t st) {
+    JobDyn d{};
+    if (dyn) d = *dyn;
+    job_write_kernel<<<1, 32, 0, st>>>(dst, job, dyn_dst, d, dyn != nullptr);
     return cudaGetLastError();
 }
 
@@ -1008,25 +1064,16 @@ cudaError_t launch_kl_raw(const tsne_csr& P, const float* Y, int64_t N, int s,
     return cudaGetLastError();
 }
 
-cudaError_t launch_kl(tsne_plan* pl, const tsne_csr& P, const float* Y) {
-    const int g = 4 * pl->sm_count;  // kl_partial holds 2 doubles per block
-    pl->launches += 1;
-    return launch_kl_raw(P, Y, pl->N, pl->s, &pl->params->Z, 0.0, pl->kl_partial, pl->tickets + 3,
-                         pl->kl_out_dev, g, pl->stream);
-}
-
-cudaError_t launch_validate(tsne_plan* pl, const tsne_csr& P) {
-    const int g = grid_for(pl, pl->N, 256, 8);
-    validate_kernel<<<g, 256, 0, pl->stream>>>(P.row_ptr, P.col, P.val, pl->N, P.nnz,
-                                               pl->valid_flag);
-    pl->launches += 1;
+cudaError_t launch_validate(const tsne_csr& P, int64_t N, int32_t* flag, int sm_count,
+                            cudaStream_t st) {
+    const int g = grid_cap(N, 256, 8LL * sm_count);
+    validate_kernel<<<g, 256, 0, st>>>(P.row_ptr, P.col, P.val, N, P.nnz, flag);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill(tsne_plan* pl, float* a, float v, int64_t n) {
-    const int g = grid_for(pl, n, 256, 8);
-    fill_kernel<<<g, 256, 0, pl->stream>>>(a, v, n);
-    pl->launches += 1;
+cudaError_t launch_fill(float* a, float v, int64_t n, int sm_count, cudaStream_t st) {
+    const int g = grid_cap(n, 256, 8LL * sm_count);
+    fill_kernel<<<g, 256, 0, st>>>(a, v, n);
     return cudaGetLastError();
 }
 

@@ -3,8 +3,7 @@
 // The attraction reads y_j for every stored p_ij: ~150 random 8-byte reads
 // per point per iteration, each one L1TEX request. Relabelling the points so
 // that neighbours in P get nearby labels turns most of these reads into
-// cache hits of the CTA's working set (and, with the window variant of the
-// force kernel, into shared-memory reads). Neighbours in P are
+// cache hits of the CTA's working set. Neighbours in P are
 // close in the embedding once the clusters have formed, so the new labels
 // follow a Morton (Z-order) curve over a 1024 x 1024 grid on the current
 // box (1-D: 2^20 cells), ties broken by the original label: a deterministic
@@ -187,41 +186,21 @@ __global__ void scan_pass2_kernel(int32_t* __restrict__ out, int64_t N,
 }
 
 // Relabelled rows: warp per new row k copies row perm[k] of P, columns mapped
-// through inv; per 256-row chunk, the mean new column index (the centre of
-// the window the force kernel stages).
+// through inv.
 __global__ void __launch_bounds__(256)
 relabel_csr_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                    const float* __restrict__ val, const int32_t* __restrict__ perm,
                    const int32_t* __restrict__ inv, const int32_t* __restrict__ rp2, int64_t N,
-                   int32_t* __restrict__ col2, float* __restrict__ val2,
-                   unsigned long long* __restrict__ chunk_sum) {
+                   int32_t* __restrict__ col2, float* __restrict__ val2) {
     const int lane = threadIdx.x % 32;
     const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; k < N; k += nwarp) {
         const int o = perm[k];
         const int s0 = row_ptr[o], s1 = row_ptr[o + 1], d0 = rp2[k];
-        unsigned long long sum = 0;
         for (int t = lane; t < s1 - s0; t += 32) {
-            const int c2 = inv[col[s0 + t]];
-            col2[d0 + t] = c2;
+            col2[d0 + t] = inv[col[s0 + t]];
             val2[d0 + t] = val[s0 + t];
-            sum += (unsigned long long)c2;
         }
-#pragma unroll
-        for (int o2 = 16; o2 >= 1; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
-        if (lane == 0) atomicAdd(&chunk_sum[k / kForceChunk], sum);
-    }
-}
-
-__global__ void chunk_centre_kernel(const unsigned long long* __restrict__ chunk_sum,
-                                    const int32_t* __restrict__ rp2, int64_t N, int nchunks,
-                                    int32_t* __restrict__ centre) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
-        const int64_t r0 = (int64_t)c * kForceChunk;
-        const int64_t r1 = (r0 + kForceChunk < N) ? r0 + kForceChunk : N;
-        const int64_t cnt = (int64_t)rp2[r1] - rp2[r0];
-        centre[c] = cnt > 0 ? (int32_t)(chunk_sum[c] / (unsigned long long)cnt)
-                            : (int32_t)((r0 + r1) / 2);
     }
 }
 
@@ -241,9 +220,9 @@ cudaError_t launch_relabel(tsne_plan* pl, const tsne_csr& P, const float* Y_cur,
     while (M < N) M <<= 1;
     const int g = grid_for_n(pl, M, 256);
     if (pl->s == 2)
-        relabel_keys_kernel<2><<<g, 256, 0, st>>>(Y_cur, pl->perm, pl->reordered, N, M, pl->params, pl->sort_keys);
+        relabel_keys_kernel<2><<<g, 256, 0, st>>>(Y_cur, pl->perm, pl->reordered, N, M, pl->host_job.params, pl->sort_keys);
     else
-        relabel_keys_kernel<1><<<g, 256, 0, st>>>(Y_cur, pl->perm, pl->reordered, N, M, pl->params, pl->sort_keys);
+        relabel_keys_kernel<1><<<g, 256, 0, st>>>(Y_cur, pl->perm, pl->reordered, N, M, pl->host_job.params, pl->sort_keys);
     pl->launches += 1;
     for (int64_t k = 2; k <= M; k <<= 1)
         for (int64_t j = k >> 1; j > 0; j >>= 1) {
@@ -259,14 +238,11 @@ cudaError_t launch_relabel(tsne_plan* pl, const tsne_csr& P, const float* Y_cur,
     std::swap(pl->inv, pl->inv_next);
     // relabelled P
     const int nb = (int)((N + 2047) / 2048);
-    scan_pass1_kernel<<<nb, 1024, 0, st>>>(pl->row_len, N, pl->rp2, pl->scan_bsum, pl->tickets + 4);
+    scan_pass1_kernel<<<nb, 1024, 0, st>>>(pl->row_len, N, pl->rp2, pl->scan_bsum, pl->relabel_ticket);
     scan_pass2_kernel<<<nb, 1024, 0, st>>>(pl->rp2, N, pl->scan_bsum);
-    const int nch = (int)((N + kForceChunk - 1) / kForceChunk);
-    cudaMemsetAsync(pl->chunk_sum, 0, sizeof(unsigned long long) * nch, st);
     relabel_csr_kernel<<<grid_for_n(pl, N * 32, 256), 256, 0, st>>>(
-        P.row_ptr, P.col, P.val, pl->perm, pl->inv, pl->rp2, N, pl->col2, pl->val2, pl->chunk_sum);
-    chunk_centre_kernel<<<(nch + 255) / 256, 256, 0, st>>>(pl->chunk_sum, pl->rp2, N, nch, pl->chunk_centre);
-    pl->launches += 4;
+        P.row_ptr, P.col, P.val, pl->perm, pl->inv, pl->rp2, N, pl->col2, pl->val2);
+    pl->launches += 3;
     // run state to the new labels
     const int64_t ns = N * pl->s;
     if (pl->s == 2) {
