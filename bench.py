@@ -9,7 +9,19 @@ region is the whole 1000-iteration job of the N = 1,000,000, s = 2 workload
 first on a scratch copy of the same job.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload n1m_2d|n1m_1d|n100k_2d|n2k_2d]
+                  [--workload n1m_2d|n1m_1d|n100k_2d|n2k_2d|served]
+
+The same JSON line also carries two sub-measurements of the batched forms:
+  "batched": 64 independent jobs (N log-uniform in [1k, 200k], s = 2, 1000
+             iterations each), run as one batch (one launch per phase for
+             all jobs, one CUDA graph per iteration, autotuned) and as a plain
+             one-plan-at-a-time loop: embeddings/s of both and the largest
+             relative difference of the jobs' final KL.
+  "served":  a bounded sample (the first jobs) of the served stream: Poisson
+             arrivals at 4/s, N log-uniform in [500, 500k], s in {1, 2},
+             perplexity in {10, 30, 50}, 1000 iterations each, admitted
+             under a 40 GB HBM budget; p50/p99 latency and embeddings/s.
+             --workload served runs the whole 500-job stream instead.
 
 Under torchrun each rank runs its own independent job (its own seed): the
 method shards by job with no data-path exchange, so scaling is weak and
@@ -225,6 +237,123 @@ def run_reference(a):
     return 0
 
 
+def batched_jobs(n_jobs: int, seed: int = 4000):
+    """Workload 4: n_jobs mixtures (10-30 clusters, Dirichlet sizes), N
+    log-uniform in [1k, 200k], perplexity 30, k = 90, Y0 ~ N(0, 1e-4)."""
+    import torch
+    from paper_1712_09005_gb300 import inputs
+    sizes = inputs.log_uniform_sizes(n_jobs, 1000, 200_000, seed=seed)
+    jobs = []
+    for j, N in enumerate(sizes):
+        args = inputs.mixture_args(4, job=j, N=int(N))
+        P = inputs.affinities(inputs.mixture(**args), 30.0, device="cuda")
+        jobs.append((P, inputs.initial_embedding(int(N), 2, seed=args["seed"])))
+    torch.cuda.empty_cache()
+    return jobs
+
+
+def run_batched_compare(n_jobs: int, n_iter: int):
+    """Embeddings/s of one batch vs a plain loop of plans, same jobs, same schedule."""
+    import torch
+    import paper_1712_09005_gb300 as pkg
+    jobs = batched_jobs(n_jobs)
+    sched = pkg.Schedule(n_iter=n_iter)
+    Pds = [pkg.DeviceCSR.from_host(*P.as_tuple()) for P, _ in jobs]
+    # a plain one-job-at-a-time loop: one plan per job (allocated before the clock)
+    plans = [pkg.Plan(P.N, 2) for P, _ in jobs]
+    Ys = [torch.as_tensor(Y0.copy(), device="cuda") for _, Y0 in jobs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for plan, Pd, Y in zip(plans, Pds, Ys):
+        plan.run(Pd, Y, sched, want_kl=False)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    kl_seq = [plan.kl(Pd, Y) for plan, Pd, Y in zip(plans, Pds, Ys)]
+    launches_seq = sum(pl.launch_count() for pl in plans)
+    for pl in plans:
+        pl.close()
+    del plans, Ys
+    torch.cuda.empty_cache()
+    with pkg.Batch(2, max_jobs=max(64, n_jobs)) as b:
+        ids = [b.add(Pd, torch.as_tensor(Y0, device="cuda"), sched) for Pd, (_, Y0) in zip(Pds, jobs)]
+        tuning = b.autotune(iters=3)  # restores every job's state afterwards
+        b.poll()
+        l0 = b.launch_count()
+        t0 = time.perf_counter()
+        b.iterate(n_iter)
+        it, st = b.poll()
+        t_bat = time.perf_counter() - t0
+        launches_bat = b.launch_count() - l0
+        assert all(it[j] == n_iter and st[j] == 0 for j in ids)
+        kl_bat = [b.kl(j) for j in ids]
+    rel = [abs(x - y) / abs(y) for x, y in zip(kl_bat, kl_seq)]
+    sumN = int(sum(P.N for P, _ in jobs))
+    return {
+        "jobs": n_jobs, "sum_N": sumN, "iterations": n_iter, "s": 2,
+        "embeddings_per_s": n_jobs / t_bat,
+        "sequential_embeddings_per_s": n_jobs / t_seq,
+        "speedup": t_seq / t_bat,
+        "point_iterations_per_s": sumN * n_iter / t_bat,
+        "kl_max_rel_diff": max(rel), "kl_mean": float(np.mean(kl_bat)),
+        "tuning": {"chunk": tuning.chunk, "fft_threads": tuning.fft_threads,
+                   "n_int_policy": "fill" if tuning.n_int_policy == 1 else "rule",
+                   "ms_per_iter": tuning.ms_per_iter},
+        "gpu_launches_batched": launches_bat, "gpu_launches_sequential": launches_seq,
+        "timing": "wall clock around the whole runs, device synchronised",
+        "workload": "N log-uniform in [1k, 200k], 10-30-cluster Gaussian mixtures in 50-d, "
+                    "perplexity 30, k=90; one batch (graph per iteration, autotuned) vs a "
+                    "loop of plans",
+    }
+
+
+def served_requests(n_take: int, n_stream: int = 500, seed: int = 5000):
+    """Workload 5: a Poisson stream (4/s) of n_stream jobs, N log-uniform in
+    [500, 500k], s in {1, 2}, perplexity in {10, 30, 50}, 1000 iterations;
+    the first n_take requests with their P built (P is ready on arrival)."""
+    import paper_1712_09005_gb300 as pkg
+    from paper_1712_09005_gb300 import inputs
+    from paper_1712_09005_gb300.serve import Request, poisson_arrivals
+    sizes = inputs.log_uniform_sizes(n_stream, 500, 500_000, seed=seed)
+    arr = poisson_arrivals(n_stream, 4.0, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    s_of = rng.integers(1, 3, size=n_stream)
+    perp_of = rng.choice([10.0, 30.0, 50.0], size=n_stream)
+    out = []
+    for i in range(n_take):
+        N = int(sizes[i])
+        args = inputs.mixture_args(5, job=i, N=N)
+        P = inputs.affinities(inputs.mixture(**args), float(perp_of[i]), device="cuda")
+        Y0 = inputs.initial_embedding(N, int(s_of[i]), seed=args["seed"])
+        out.append(Request(i, float(arr[i]), int(s_of[i]), P.row_ptr, P.col, P.val, Y0,
+                           pkg.Schedule(n_iter=1000)))
+    import torch
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_served(n_take: int, n_stream: int = 500):
+    from paper_1712_09005_gb300.serve import Server
+    reqs = served_requests(n_take, n_stream)
+    srv = Server(budget_bytes=40 * 10 ** 9, max_jobs=64, iters_per_round=25)
+    try:
+        out = srv.serve(reqs)
+    finally:
+        srv.close()
+    res = out["results"]
+    ok = sum(1 for r in res if r.status == 0)
+    return {
+        "jobs": len(res), "ok": ok, "p50_latency_s": out["p50_s"], "p99_latency_s": out["p99_s"],
+        "embeddings_per_s": out["embeddings_per_s"], "makespan_s": out["makespan_s"],
+        "peak_resident_bytes": out["peak_bytes"], "budget_bytes": 40 * 10 ** 9,
+        "point_iterations": int(sum(r.N for r in res)) * 1000,
+        "sample": (f"the first {n_take} of the {n_stream}-job stream" if n_take < n_stream
+                   else f"the whole {n_stream}-job stream"),
+        "workload": "Poisson arrivals 4/s, N log-uniform [500, 500k], s in {1,2}, perplexity "
+                    "{10,30,50}, 1000 iterations, 40 GB budget; latency = arrival to "
+                    "embedding in host memory",
+    }
+
+
 def run_ours(a):
     import torch
     import paper_1712_09005_gb300 as pkg
@@ -337,6 +466,15 @@ def run_ours(a):
                "sample": f"{it} oracle iterations (FP64 interpolated gradient with radix-2 FFT + "
                          f"update) of this job from Y0, {dt:.1f} s"}
 
+    batched = served = None
+    plan.close()
+    del Pd
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not a.no_batched:
+        batched = run_batched_compare(a.batched_jobs, 1000)
+    if rank == 0 and world == 1 and not a.no_served:
+        served = run_served(a.served_jobs)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -358,11 +496,29 @@ def run_ours(a):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_served_only(a):
+    """--workload served: the whole 500-job stream (rank 0 only)."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1712_09005_gb300 import build as pbuild
+    pbuild.build()
+    served = run_served(500)
+    line = {"metric": "served p50/p99 latency (FIt-SNE jobs)", "value": served["p99_latency_s"],
+            "unit": "s (p99)", "n_gpus": 1, "higher_is_better": False, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": served["workload"]}, "served": served}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -372,16 +528,23 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="n1m_2d")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served"], default="n1m_2d")
     ap.add_argument("--n", type=int, default=0, help="override the workload's N (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--batched-jobs", type=int, default=64)
+    ap.add_argument("--served-jobs", type=int, default=40,
+                    help="requests of the served stream in the default run's sample")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle iterations the reference arm times")
     a = ap.parse_args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "served":
+        return run_served_only(a)
     return run_ours(a)
 
 

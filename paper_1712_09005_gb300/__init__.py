@@ -369,6 +369,15 @@ class Batch:
         self._P[jid] = (P, Y0)
         return jid
 
+    def upload(self, req):
+        """Copies a request's host CSR and Y0 to the device on the batch's
+        stream (pinned staging, asynchronous)."""
+        with torch.cuda.stream(self._ext):
+            up = lambda a: torch.from_numpy(a).pin_memory().to("cuda", non_blocking=True)
+            P = DeviceCSR(up(req.row_ptr), up(req.col), up(req.val))
+            Y0 = up(req.Y0)
+        return P, Y0
+
     def remove(self, job: int):
         tsne_batch_remove_job(self.handle, job)
         self.N.pop(job, None)
