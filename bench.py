@@ -376,7 +376,7 @@ def run_ours(a):
     P, Y0 = make_inputs(a.workload, rank, "cuda", N)
     Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
     stream = torch.cuda.current_stream()
-    plan = pkg.Plan(N, s, n_intervals=fixed, stream=stream.cuda_stream)
+    plan = pkg.Plan(N, s, n_intervals=fixed, stream=stream.cuda_stream, force_mode=a.force_mode)
 
     # warm-up on a scratch copy of the job
     Yw = torch.as_tensor(Y0.copy(), device="cuda")
@@ -533,6 +533,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--force-mode", type=int, default=0,
+                    help="force-kernel schedule: 0 auto, 1 grid, 2 region (profiling)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--batched-jobs", type=int, default=64)

@@ -71,7 +71,19 @@ typedef struct {
     void* stream;      /* cudaStream_t for all work; NULL = the legacy default stream */
     int32_t relabel_first; /* iteration of a run's first locality relabelling [100]; < 0: never */
     int32_t relabel_every; /* iterations between later relabellings [300] */
+    int32_t force_mode;    /* work schedule of the force kernel, TSNE_FORCE_* [TSNE_FORCE_AUTO] */
 } tsne_plan_opts;
+
+/* Work schedules of the force kernel (same arithmetic, bitwise equal results):
+ * GRID    a grid-stride loop over chunks of 256 rows;
+ * REGION  the 32-row blocks are cut into one contiguous region per SM; an
+ *         SM's warps take their own region's blocks first (so, in a
+ *         relabelled run, they gather neighbours from one working set that
+ *         stays in the SM's L1), then help the regions still in progress;
+ * AUTO    REGION (a plan's steps and gradients; batches use GRID). */
+#define TSNE_FORCE_AUTO 0
+#define TSNE_FORCE_GRID 1
+#define TSNE_FORCE_REGION 2
 
 /* Gradient-descent schedule (Sec. 1.2 early exaggeration, Sec. 4 late
  * exaggeration). The momentum/gain update is not specified by the paper; the
@@ -189,6 +201,7 @@ int tsne_run(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
  * neighbouring y_j hit nearby memory (cache reuse). The gradient is unchanged up to
  * the order of each row's attraction sum; Y is returned in the caller's
  * labels. P must stay the same across the tsne_run_iters calls of one run.
+
  */
 int tsne_run_reset(tsne_plan* plan);
 int tsne_run_iters(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,

@@ -97,10 +97,10 @@ def _vec(t: torch.Tensor, N: int, s: int, name: str):
 
 def tsne_plan_create(N: int, s: int, n_intervals: int = 0, p: int = 3, n_min: int = 0,
                      n_int_max: int = 0, stream: int | None = None, relabel_first: int = 0,
-                     relabel_every: int = 0) -> ctypes.c_void_p:
+                     relabel_every: int = 0, force_mode: int = 0) -> ctypes.c_void_p:
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    opts = _abi.tsne_plan_opts(n_min, n_int_max, stream, relabel_first, relabel_every)
+    opts = _abi.tsne_plan_opts(n_min, n_int_max, stream, relabel_first, relabel_every, force_mode)
     out = ctypes.c_void_p()
     check(lib().tsne_plan_create(N, s, n_intervals, p, ctypes.byref(opts), ctypes.byref(out)))
     return out
@@ -421,10 +421,10 @@ class Plan:
 
     def __init__(self, N: int, s: int, n_intervals: int = 0, p: int = 3, n_min: int = 0,
                  n_int_max: int = 0, stream: int | None = None, relabel_first: int = 0,
-                 relabel_every: int = 0):
+                 relabel_every: int = 0, force_mode: int = 0):
         self.N, self.s = N, s
         self.handle = tsne_plan_create(N, s, n_intervals, p, n_min, n_int_max, stream,
-                                       relabel_first, relabel_every)
+                                       relabel_first, relabel_every, force_mode)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

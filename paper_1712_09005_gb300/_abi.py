@@ -39,7 +39,7 @@ class tsne_csr(ctypes.Structure):
 class tsne_plan_opts(ctypes.Structure):
     _fields_ = [("n_min", ctypes.c_int32), ("n_int_max", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("relabel_first", ctypes.c_int32),
-                ("relabel_every", ctypes.c_int32)]
+                ("relabel_every", ctypes.c_int32), ("force_mode", ctypes.c_int32)]
 
 
 class tsne_step_params(ctypes.Structure):
@@ -57,6 +57,10 @@ class tsne_plan_info_t(ctypes.Structure):
                 ("fft_len", ctypes.c_int32), ("n_chunks", ctypes.c_int32),
                 ("Z", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
+
+TSNE_FORCE_AUTO = 0
+TSNE_FORCE_GRID = 1
+TSNE_FORCE_REGION = 2
 
 TSNE_NINT_RULE = 0
 TSNE_NINT_FILL = 1

@@ -307,7 +307,7 @@ void free_plan(tsne_plan* pl) {
                     pl->h_row_ptr, pl->h_col,      pl->h_val,     pl->h_Y,        pl->perm,
                     pl->inv,       pl->perm_next,  pl->inv_next,  pl->row_len,    pl->cur_of,
                     pl->rp2,       pl->col2,       pl->val2,      pl->sort_keys,  pl->scan_bsum,
-                    pl->relabel_ticket, pl->tmp_state, pl->y_cur};
+                    pl->relabel_ticket, pl->tmp_state, pl->y_cur, pl->region_next};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete pl;
@@ -381,7 +381,13 @@ int enqueue_field(tsne_plan* pl, bool timed) {
 }
 
 int enqueue_forces(tsne_plan* pl, int step) {
-    CU(fitsne::launch_forces(pl->d_job, pl->caps, step, pl->stream), "force kernel launch");
+    if (pl->force_mode == TSNE_FORCE_GRID) {
+        CU(fitsne::launch_forces(pl->d_job, pl->caps, step, pl->stream), "force kernel launch");
+    } else {
+        CU(fitsne::launch_forces_region(pl->d_job, pl->s, pl->p, step, pl->region_next,
+                                        pl->n_regions, pl->sm_count, pl->stream),
+           "force kernel launch");
+    }
     pl->launches += 1;
     prof_mark(pl, 4);
     return TSNE_OK;
@@ -447,6 +453,11 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     pl->fx_shift = fitsne::fixed_point_shift(N, s, p);
     pl->relabel_first = o.relabel_first == 0 ? 100 : o.relabel_first;
     pl->relabel_every = o.relabel_every > 0 ? o.relabel_every : 300;
+    pl->force_mode = o.force_mode;
+    if (pl->force_mode < TSNE_FORCE_AUTO || pl->force_mode > TSNE_FORCE_REGION) {
+        free_plan(pl);
+        return set_error(TSNE_ERR_INVALID_ARG, "unknown force_mode %d", o.force_mode);
+    }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -487,6 +498,7 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     ALLOC(relabel_ticket, 1);
     ALLOC(tmp_state, N * s);
     ALLOC(y_cur, N * s);
+    ALLOC(region_next, 1024);
 #undef ALLOC
     if (rc != TSNE_OK) { free_plan(pl); return rc; }
 
@@ -520,6 +532,14 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     if (ce == cudaSuccess) ce = cudaMemsetAsync(pl->kl_ticket, 0, sizeof(unsigned), st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(pl->relabel_ticket, 0, sizeof(unsigned), st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(pl->d_dyn, 0, sizeof(JobDyn), st);
+    if (ce == cudaSuccess) {
+        // the SM id range sizes the region schedule of the force kernel
+        int* d = reinterpret_cast<int*>(pl->region_next);
+        ce = fitsne::query_sm_id_count(d, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&pl->n_regions, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce == cudaSuccess && (pl->n_regions < 1 || pl->n_regions > 1023)) pl->n_regions = pl->sm_count;
+    }
     if (ce == cudaSuccess) ce = fitsne::fft_configure(s, pl->fft.L_max);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { free_plan(pl); return cuda_fail(ce, "plan initialisation"); }

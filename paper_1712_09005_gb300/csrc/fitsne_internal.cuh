@@ -244,6 +244,10 @@ struct tsne_plan {
     unsigned* relabel_ticket;  // [1]
     float* tmp_state;        // [N * s]
     float* y_cur;            // [N * s] run state Y in the relabelled order
+    // force kernel scheduling
+    int force_mode;          // TSNE_FORCE_* (plan option)
+    int n_regions;           // SM id range of the device
+    unsigned* region_next;   // [n_regions + 1] block counters of the region-scheduled kernel, claimed total
     // host-buffer path (tsne_run_host), allocated on first use
     int64_t host_nnz_cap;
     int32_t* h_row_ptr;
@@ -375,6 +379,12 @@ cudaError_t launch_convolution(const Job* jobs, const TableCaps& c, const Tables
                                cudaStream_t st);
 cudaError_t launch_forces(const Job* jobs, const TableCaps& c, int step, cudaStream_t st);
 cudaError_t launch_advance(const Job* jobs, int njobs, cudaStream_t st);
+// Force/update step of one job with SM-local scheduling of its 32-row blocks
+// (next: n_regions counters and the claimed total, zeroed here before the launch).
+cudaError_t launch_forces_region(const Job* jobs, int s, int p, int step, unsigned* next,
+                                 int n_regions, int sm_count, cudaStream_t st);
+// Writes the device's SM id range (%nsmid) to out_dev.
+cudaError_t query_sm_id_count(int* out_dev, cudaStream_t st);
 // Stream-ordered write of one table row (and, if dyn is not NULL, its JobDyn)
 // through a kernel argument: no host staging buffer outlives the call.
 cudaError_t launch_job_write(Job* dst, const Job& job, JobDyn* dyn_dst, const JobDyn* dyn,

@@ -645,6 +645,7 @@ __device__ __forceinline__ float update_one(float y, float dy, float& u, float& 
     return y + u;
 }
 
+// One attraction term p_ij (y_i - y_j) / (1 + |y_i - y_j|^2) added to (a0, a1).
 template <int S>
 __device__ __forceinline__ void attract(float yi0, float yi1, int j, float v,
                                         const float* __restrict__ Y, float& a0, float& a1) {
@@ -660,58 +661,247 @@ __device__ __forceinline__ void attract(float yi0, float yi1, int j, float v,
     }
 }
 
-template <int U>
-__device__ __forceinline__ void load_slots(const int32_t* __restrict__ col,
-                                           const float* __restrict__ val, int beg, int end,
-                                           int lane, int (&jj)[U], float (&vv)[U]) {
+// Rows are taken kRowLanes lanes at a time (32 / kRowLanes rows per warp
+// step; 32 measured fastest on GB300). Entries of one row [beg, end) are
+// shared out over its lanes in windows of 4 kRowLanes: lane g of the row's
+// group takes entries beg + 4 kRowLanes w + 4 g + q (q = 0..3, those below
+// end) of window w = 0, 1, ... in that order, and the group's partial sums
+// are combined by an xor tree over its lanes. The order depends only on the
+// row's own entries (not on where the row sits in memory), so every force
+// kernel, and a relabelled copy of P whose rows keep their entry order, give
+// bitwise equal row sums. RowBuf holds the first W windows of a lane's row,
+// loaded ahead of use.
+#ifndef FITSNE_ROW_LANES
+#define FITSNE_ROW_LANES 32
+#endif
+constexpr int kRowLanes = FITSNE_ROW_LANES;
+static_assert(kRowLanes == 8 || kRowLanes == 16 || kRowLanes == 32, "lanes per row");
+
+template <int W>
+struct RowBuf {
+    int c[4 * W];
+    float v[4 * W];
+    int beg, end;
+};
+
+// Masked streaming loads of the first W windows of a row; g: the lane's
+// index in its row group.
+template <int W>
+__device__ __forceinline__ void row_load(RowBuf<W>& b, const int32_t* __restrict__ col,
+                                         const float* __restrict__ val, int beg, int end, int g) {
+    b.beg = beg;
+    b.end = end;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int e = beg + lane + 32 * u;
-        jj[u] = e < end ? __ldcs(&col[e]) : 0;
-        vv[u] = e < end ? __ldcs(&val[e]) : 0.0f;
-    }
+    for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = beg + 4 * kRowLanes * w + 4 * g + q;
+            const bool in = e < end;
+            b.c[4 * w + q] = in ? __ldcs(&col[e]) : 0;
+            b.v[4 * w + q] = in ? __ldcs(&val[e]) : 0.0f;
+        }
 }
 
-// Attraction of one row from its prefetched entries (and any beyond 32 U),
-// summed over the warp.
-template <int S, int U>
-__device__ __forceinline__ void attract_row(const int32_t* __restrict__ col,
+// This lane's share of the attraction of the row held in b (and of the
+// row's windows beyond W), not yet combined over the row's lanes.
+template <int S, int W>
+__device__ __forceinline__ void row_attract(const RowBuf<W>& b, const int32_t* __restrict__ col,
                                             const float* __restrict__ val,
-                                            const float* __restrict__ Y, int beg, int end,
-                                            float yi0, float yi1, int lane, const int (&jj)[U],
-                                            const float (&vv)[U], float& a0, float& a1) {
+                                            const float* __restrict__ Y, float yi0, float yi1,
+                                            int g, float& a0, float& a1) {
     a0 = 0.0f;
     a1 = 0.0f;
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-        if (beg + lane + 32 * u < end) attract<S>(yi0, yi1, jj[u], vv[u], Y, a0, a1);
-    for (int e = beg + lane + 32 * U; e < end; e += 32)
-        attract<S>(yi0, yi1, __ldcs(&col[e]), __ldcs(&val[e]), Y, a0, a1);
-    a0 = warp_sum(a0);
-    if (S == 2) a1 = warp_sum(a1);
+    for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = b.beg + 4 * kRowLanes * w + 4 * g + q;
+            if (e < b.end) attract<S>(yi0, yi1, b.c[4 * w + q], b.v[4 * w + q], Y, a0, a1);
+        }
+#pragma unroll 2
+    for (int wb = b.beg + 4 * kRowLanes * W; wb < b.end; wb += 4 * kRowLanes) {
+        int c[4];
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = wb + 4 * g + q;
+            const bool in = e < b.end;
+            c[q] = in ? __ldcs(&col[e]) : 0;
+            v[q] = in ? __ldcs(&val[e]) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (wb + 4 * g + q < b.end) attract<S>(yi0, yi1, c[q], v[q], Y, a0, a1);
+    }
+}
+
+// Sum over the lanes of a row group (xor tree inside aligned groups).
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = kRowLanes / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+#ifndef FITSNE_FORCE_WINDOWS
+#define FITSNE_FORCE_WINDOWS 1  // windows of a row loaded ahead
+#endif
+#ifndef FITSNE_FORCE_DEPTH
+#define FITSNE_FORCE_DEPTH 2    // row steps whose windows are in flight
+#endif
+#ifndef FITSNE_FORCE_MINB
+#define FITSNE_FORCE_MINB 4     // resident 256-thread blocks per SM the registers must allow
+#endif
+
+// Points i0 .. i0 + 31 (fewer at the end) of job J, one warp:
+//  1. lane l takes point i0 + l: its row bounds, coordinates, its box, local
+//     coordinates and Lagrange weights, and the Step 3 interpolation of the
+//     node values of its box -> F_rep;
+//  2. the warp walks the 32 rows of P; each row's entries are spread over
+//     the lanes, and row r + 1's entries are loaded before row r's are used;
+//     the row sum lands in lane r;
+//  3. lane l forms dY (or the update) of its point; the job's output pointers
+//     and schedule values are read only now; stores are coalesced.
+template <int S, int PP, bool STEP>
+__device__ __forceinline__ void force_block(const Job& J, const Params* __restrict__ Pp,
+                                            const float* __restrict__ Y, int64_t i0, int64_t N,
+                                            int lane) {
+    constexpr int W = FITSNE_FORCE_WINDOWS;
+    constexpr int DEPTH = FITSNE_FORCE_DEPTH;
+    const int32_t* __restrict__ col = J.col;
+    const float* __restrict__ val = J.val;
+    const int64_t i = i0 + lane;
+    const bool live = i < N;
+    const int nrows = (N - i0) < 32 ? (int)(N - i0) : 32;
+    // 1. per-point work, one point per lane
+    int rp_lo = 0, rp_hi = 0;
+    float yi0 = 0.0f, yi1 = 0.0f, f0 = 0.0f, f1 = 0.0f;
+    if (live) {
+        const int32_t* __restrict__ row_ptr = J.row_ptr;
+        rp_lo = __ldg(&row_ptr[i]);
+        rp_hi = __ldg(&row_ptr[i + 1]);
+        if (S == 2) {
+            const float2 t = reinterpret_cast<const float2*>(Y)[i];
+            yi0 = t.x;
+            yi1 = t.y;
+        } else {
+            yi0 = Y[i];
+        }
+        // Step 3: (h_{m+1} - y(m) h_{s+2})(y_i) = delta sum_g L_g [u'_m + (j_m + 1/2 - t_m) v]
+        const Params& P = *Pp;
+        const float4* __restrict__ hgrid = J.hgrid;
+        const int n = P.n;
+        const int l1 = interval_of(yi0, P);
+        const float t1 = local_t(yi0, l1, P);
+        float L1[PP];
+        lagrange<PP>(t1, L1);
+        if (S == 2) {
+            const int l2 = interval_of(yi1, P);
+            const float t2 = local_t(yi1, l2, P);
+            float L2[PP];
+            lagrange<PP>(t2, L2);
+#pragma unroll
+            for (int j1 = 0; j1 < PP; ++j1) {
+                const float4* row = hgrid + (int64_t)(l1 * PP + j1) * n + l2 * PP;
+                const float o1 = ((float)j1 + 0.5f) - t1;
+#pragma unroll
+                for (int j2 = 0; j2 < PP; ++j2) {
+                    const float4 h = __ldg(row + j2);  // (h1, u'1, u'2, v)
+                    const float wt = L1[j1] * L2[j2];
+                    const float o2 = ((float)j2 + 0.5f) - t2;
+                    f0 += wt * __fmaf_rn(o1, h.w, h.y);
+                    f1 += wt * __fmaf_rn(o2, h.w, h.z);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j1 = 0; j1 < PP; ++j1) {
+                const float4 h = __ldg(hgrid + l1 * PP + j1);
+                f0 += L1[j1] * __fmaf_rn(((float)j1 + 0.5f) - t1, h.w, h.y);
+            }
+        }
+    }
+    // 2. attraction: each warp step takes 32 / kRowLanes rows (lane group g
+    //    of the step works on row step * RPW + lane / kRowLanes); DEPTH steps'
+    //    entries are in flight; a row's sum is handed to the lane of its point
+    constexpr int RPW = 32 / kRowLanes;
+    const int sub = lane / kRowLanes, g = lane % kRowLanes;
+    const int nsteps = (nrows + RPW - 1) / RPW;
+    float A0 = 0.0f, A1 = 0.0f;
+    RowBuf<W> buf[DEPTH];
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d) {
+        const int r = d * RPW + sub;
+        const int rs = r < nrows ? r : 0;
+        const int bg = __shfl_sync(kFull, rp_lo, rs), en = __shfl_sync(kFull, rp_hi, rs);
+        if (d < nsteps) row_load<W>(buf[d], col, val, bg, r < nrows ? en : bg, g);
+    }
+    for (int s0 = 0; s0 < nsteps; s0 += DEPTH) {
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            const int st = s0 + d;
+            if (st < nsteps) {
+                const int r = st * RPW + sub;
+                const int rs = r < nrows ? r : 0;
+                const float y0 = __shfl_sync(kFull, yi0, rs), y1 = __shfl_sync(kFull, yi1, rs);
+                float a0, a1;
+                row_attract<S, W>(buf[d], col, val, Y, y0, y1, g, a0, a1);
+                a0 = group_sum(a0);
+                if (S == 2) a1 = group_sum(a1);
+                const int from = (lane - st * RPW) * kRowLanes;  // group of this lane's row
+                const float t0 = __shfl_sync(kFull, a0, from & 31), t1 = __shfl_sync(kFull, a1, from & 31);
+                if (lane >= st * RPW && lane < st * RPW + RPW) { A0 = t0; A1 = t1; }
+                const int sn = st + DEPTH;
+                if (sn < nsteps) {
+                    const int rn = sn * RPW + sub;
+                    const int rns = rn < nrows ? rn : 0;
+                    const int bg = __shfl_sync(kFull, rp_lo, rns), en = __shfl_sync(kFull, rp_hi, rns);
+                    row_load<W>(buf[d], col, val, bg, rn < nrows ? en : bg, g);
+                }
+            }
+        }
+    }
+    // 3. gradient (and update) of this lane's point
+    if (live) {
+        const Params& P = *Pp;
+        const float fs = P.delta * P.inv_Z;
+        const float alpha = P.alpha;
+        const float g0 = 4.0f * (alpha * A0 + f0 * fs);
+        const float g1 = (S == 2) ? 4.0f * (alpha * A1 + f1 * fs) : 0.0f;
+        if (!STEP) {
+            float* __restrict__ dY = J.dY;
+            if (S == 2) reinterpret_cast<float2*>(dY)[i] = make_float2(g0, g1);
+            else dY[i] = g0;
+        } else {
+            const StepArgs sa{J.ybuf[P.cur ^ 1], J.uY, J.gains, P.momentum, J.lr, J.min_gain,
+                              J.gain_inc, J.gain_dec};
+            float2 us, gs;
+            if (S == 2) {
+                us = reinterpret_cast<const float2*>(sa.uY)[i];
+                gs = reinterpret_cast<const float2*>(sa.gains)[i];
+            } else {
+                us = make_float2(sa.uY[i], 0.0f);
+                gs = make_float2(sa.gains[i], 0.0f);
+            }
+            const float n0 = update_one(yi0, g0, us.x, gs.x, sa);
+            if (S == 2) {
+                const float n1 = update_one(yi1, g1, us.y, gs.y, sa);
+                reinterpret_cast<float2*>(sa.uY)[i] = us;
+                reinterpret_cast<float2*>(sa.gains)[i] = gs;
+                reinterpret_cast<float2*>(sa.Y_new)[i] = make_float2(n0, n1);
+            } else {
+                sa.uY[i] = us.x;
+                sa.gains[i] = gs.x;
+                sa.Y_new[i] = n0;
+            }
+        }
+    }
 }
 
 // A work item is a chunk of kForceChunk = 256 consecutive points (rows of P)
 // of one job; warp w of the CTA owns rows 32 w .. 32 w + 31 of the chunk.
-// Per 32-row block:
-//  1. lane l takes point i0 + l: its row bounds, coordinates, optimizer state
-//     (coalesced), its box, local coordinates and Lagrange weights, and the
-//     Step 3 interpolation of the node values of its box -> F_rep;
-//  2. the warp walks the 32 rows of P; each row's entries are spread over
-//     the lanes, and row r + 1's entries are loaded before row r's are used;
-//     the row sum lands in lane r;
-//  3. lane l forms dY (or the update) of its point; stores are coalesced.
-#ifndef FITSNE_FORCE_SLOTS
-#define FITSNE_FORCE_SLOTS 6  // prefetched entries per lane per row
-#endif
-#ifndef FITSNE_FORCE_MINB
-#define FITSNE_FORCE_MINB 4   // resident 256-thread blocks per SM the registers must allow
-#endif
-
 template <int S, int PP, bool STEP>
 __global__ void __launch_bounds__(256, FITSNE_FORCE_MINB)
 force_kernel(const Job* __restrict__ jobs, int njobs) {
-    constexpr int U = FITSNE_FORCE_SLOTS;
     __shared__ int32_t s_start[kMaxJobs + 1];
     const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) {
         const Params* P = J.params;
@@ -726,126 +916,66 @@ force_kernel(const Job* __restrict__ jobs, int njobs) {
         const int64_t i0 = c * kForceChunk + (threadIdx.x / 32) * 32;
         if (i0 >= N) continue;
         const Params* __restrict__ Pp = J.params;
-        const int32_t* __restrict__ col = J.col;
-        const float* __restrict__ val = J.val;
         const float* __restrict__ Y = J.ybuf[Pp->cur];
-        const int64_t i = i0 + lane;
-        const bool live = i < N;
-        const int nrows = (N - i0) < 32 ? (int)(N - i0) : 32;
-        // 1. per-point work, one point per lane
-        int rp_lo = 0, rp_hi = 0;
-        float yi0 = 0.0f, yi1 = 0.0f, f0 = 0.0f, f1 = 0.0f;
-        if (live) {
-            const int32_t* __restrict__ row_ptr = J.row_ptr;
-            rp_lo = __ldg(&row_ptr[i]);
-            rp_hi = __ldg(&row_ptr[i + 1]);
-            if (S == 2) {
-                const float2 t = reinterpret_cast<const float2*>(Y)[i];
-                yi0 = t.x;
-                yi1 = t.y;
-            } else {
-                yi0 = Y[i];
-            }
-            // Step 3: (h_{m+1} - y(m) h_{s+2})(y_i) = delta sum_g L_g [u'_m + (j_m + 1/2 - t_m) v]
-            const Params& P = *Pp;
-            const float4* __restrict__ hgrid = J.hgrid;
-            const int n = P.n;
-            const int l1 = interval_of(yi0, P);
-            const float t1 = local_t(yi0, l1, P);
-            float L1[PP];
-            lagrange<PP>(t1, L1);
-            if (S == 2) {
-                const int l2 = interval_of(yi1, P);
-                const float t2 = local_t(yi1, l2, P);
-                float L2[PP];
-                lagrange<PP>(t2, L2);
-#pragma unroll
-                for (int j1 = 0; j1 < PP; ++j1) {
-                    const float4* row = hgrid + (int64_t)(l1 * PP + j1) * n + l2 * PP;
-                    const float o1 = ((float)j1 + 0.5f) - t1;
-#pragma unroll
-                    for (int j2 = 0; j2 < PP; ++j2) {
-                        const float4 h = __ldg(row + j2);  // (h1, u'1, u'2, v)
-                        const float wt = L1[j1] * L2[j2];
-                        const float o2 = ((float)j2 + 0.5f) - t2;
-                        f0 += wt * __fmaf_rn(o1, h.w, h.y);
-                        f1 += wt * __fmaf_rn(o2, h.w, h.z);
-                    }
+        force_block<S, PP, STEP>(J, Pp, Y, i0, N, lane);
+    }
+}
+
+__device__ __forceinline__ unsigned sm_id() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned sm_id_count() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(r));
+    return r;
+}
+
+// The step (or gradient) of one job with SM-local work: the 32-row blocks
+// are cut into n_regions contiguous regions (n_regions >= the SM id range);
+// the warps resident on the SM with id r take the blocks of region r, in
+// order, through the region's counter next[r]. Rows of a relabelled run that
+// are close in label are close in the embedding and share most neighbours,
+// so all warps of an SM gather from one working set of y_j that the SM's L1
+// holds. A warp whose own region is used up moves on to regions r + 1, r + 2,
+// ... (cyclically) to help SMs that are behind, and stops as soon as the
+// count of claimed blocks (next[n_regions]) reaches the total, so the tail
+// costs no more than the last claims. The loop ends: every probe either
+// claims a block (finitely many) or moves to the next region (at most
+// n_regions moves). next[0 .. n_regions] must be zero at launch.
+template <int S, int PP, bool STEP>
+__global__ void __launch_bounds__(256, FITSNE_FORCE_MINB)
+force_region_kernel(const Job* __restrict__ jobs, unsigned* __restrict__ next, int n_regions) {
+    const Job& J = jobs[0];
+    const Params* __restrict__ Pp = J.params;
+    if (!job_live(*Pp)) return;
+    const int64_t N = J.N;
+    const float* __restrict__ Y = J.ybuf[Pp->cur];
+    const int lane = threadIdx.x % 32;
+    const int64_t nblk = (N + 31) / 32;
+    const int home = (int)(sm_id() % (unsigned)n_regions);
+    unsigned* claimed = next + n_regions;
+    for (int hop = 0; hop < n_regions;) {
+        const int r = (home + hop) % n_regions;
+        const int64_t b0 = nblk * r / n_regions, b1 = nblk * (r + 1) / n_regions;
+        int64_t blk = -1;
+        if (lane == 0) {
+            if (hop == 0 || *(volatile unsigned*)claimed < (unsigned)nblk) {
+                const unsigned k = atomicAdd(&next[r], 1u);
+                if (b0 + (int64_t)k < b1) {
+                    blk = b0 + k;
+                    atomicAdd(claimed, 1u);
                 }
             } else {
-#pragma unroll
-                for (int j1 = 0; j1 < PP; ++j1) {
-                    const float4 h = __ldg(hgrid + l1 * PP + j1);
-                    f0 += L1[j1] * __fmaf_rn(((float)j1 + 0.5f) - t1, h.w, h.y);
-                }
+                blk = -2;  // every block is claimed: done
             }
         }
-        // 2. attraction, row by row, next row's entries in flight
-        float A0 = 0.0f, A1 = 0.0f;
-        int jA[U], jB[U];
-        float vA[U], vB[U];
-        {
-            const int b0 = __shfl_sync(kFull, rp_lo, 0), e0 = __shfl_sync(kFull, rp_hi, 0);
-            load_slots<U>(col, val, b0, e0, lane, jA, vA);
-        }
-        for (int r = 0; r < nrows; r += 2) {
-            const int bA = __shfl_sync(kFull, rp_lo, r), eA = __shfl_sync(kFull, rp_hi, r);
-            const int bB = __shfl_sync(kFull, rp_lo, r + 1), eB = __shfl_sync(kFull, rp_hi, r + 1);
-            const bool hasB = r + 1 < nrows;
-            if (hasB) load_slots<U>(col, val, bB, eB, lane, jB, vB);
-            {
-                const float y0 = __shfl_sync(kFull, yi0, r), y1 = __shfl_sync(kFull, yi1, r);
-                float a0, a1;
-                attract_row<S, U>(col, val, Y, bA, eA, y0, y1, lane, jA, vA, a0, a1);
-                if (lane == r) { A0 = a0; A1 = a1; }
-            }
-            if (hasB) {
-                if (r + 2 < nrows) {
-                    const int bC = __shfl_sync(kFull, rp_lo, r + 2), eC = __shfl_sync(kFull, rp_hi, r + 2);
-                    load_slots<U>(col, val, bC, eC, lane, jA, vA);
-                }
-                const float y0 = __shfl_sync(kFull, yi0, r + 1), y1 = __shfl_sync(kFull, yi1, r + 1);
-                float a0, a1;
-                attract_row<S, U>(col, val, Y, bB, eB, y0, y1, lane, jB, vB, a0, a1);
-                if (lane == r + 1) { A0 = a0; A1 = a1; }
-            }
-        }
-        // 3. gradient (and update) of this lane's point; the job's output
-        //    pointers and schedule values are read only now
-        if (live) {
-            const Params& P = *Pp;
-            const float fs = P.delta * P.inv_Z;
-            const float alpha = P.alpha;
-            const float g0 = 4.0f * (alpha * A0 + f0 * fs);
-            const float g1 = (S == 2) ? 4.0f * (alpha * A1 + f1 * fs) : 0.0f;
-            if (!STEP) {
-                float* __restrict__ dY = J.dY;
-                if (S == 2) reinterpret_cast<float2*>(dY)[i] = make_float2(g0, g1);
-                else dY[i] = g0;
-            } else {
-                const StepArgs sa{J.ybuf[P.cur ^ 1], J.uY, J.gains, P.momentum, J.lr, J.min_gain,
-                                  J.gain_inc, J.gain_dec};
-                float2 us, gs;
-                if (S == 2) {
-                    us = reinterpret_cast<const float2*>(sa.uY)[i];
-                    gs = reinterpret_cast<const float2*>(sa.gains)[i];
-                } else {
-                    us = make_float2(sa.uY[i], 0.0f);
-                    gs = make_float2(sa.gains[i], 0.0f);
-                }
-                const float n0 = update_one(yi0, g0, us.x, gs.x, sa);
-                if (S == 2) {
-                    const float n1 = update_one(yi1, g1, us.y, gs.y, sa);
-                    reinterpret_cast<float2*>(sa.uY)[i] = us;
-                    reinterpret_cast<float2*>(sa.gains)[i] = gs;
-                    reinterpret_cast<float2*>(sa.Y_new)[i] = make_float2(n0, n1);
-                } else {
-                    sa.uY[i] = us.x;
-                    sa.gains[i] = gs.x;
-                    sa.Y_new[i] = n0;
-                }
-            }
-        }
+        blk = __shfl_sync(kFull, blk, 0);
+        if (blk == -2) break;
+        if (blk < 0) { ++hop; continue; }
+        force_block<S, PP, STEP>(J, Pp, Y, blk * 32, N, lane);
     }
 }
 
@@ -1005,6 +1135,33 @@ static void forces_impl(const Job* jobs, const TableCaps& c, int step, cudaStrea
     const int g = grid_cap(c.sum_N, kForceChunk, 8LL * c.sm_count);
     if (step) force_kernel<S, PP, true><<<g, 256, 0, st>>>(jobs, c.njobs);
     else force_kernel<S, PP, false><<<g, 256, 0, st>>>(jobs, c.njobs);
+}
+
+template <int S, int PP>
+static void region_impl(const Job* jobs, int step, unsigned* next, int n_regions, int sm_count,
+                        cudaStream_t st) {
+    const int g = FITSNE_FORCE_MINB * sm_count;
+    if (step) force_region_kernel<S, PP, true><<<g, 256, 0, st>>>(jobs, next, n_regions);
+    else force_region_kernel<S, PP, false><<<g, 256, 0, st>>>(jobs, next, n_regions);
+}
+
+cudaError_t launch_forces_region(const Job* jobs, int s, int p, int step, unsigned* next,
+                                 int n_regions, int sm_count, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned) * (n_regions + 1), st);
+    if (e != cudaSuccess) return e;
+    const TableCaps c{s, p};
+    if (s == 2) { FITSNE_DISPATCH(2, region_impl, jobs, step, next, n_regions, sm_count, st); }
+    else { FITSNE_DISPATCH(1, region_impl, jobs, step, next, n_regions, sm_count, st); }
+    return cudaGetLastError();
+}
+
+__global__ void sm_id_count_kernel(int* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = (int)sm_id_count();
+}
+
+cudaError_t query_sm_id_count(int* out_dev, cudaStream_t st) {
+    sm_id_count_kernel<<<1, 32, 0, st>>>(out_dev);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_forces(const Job* jobs, const TableCaps& c, int step, cudaStream_t st) {

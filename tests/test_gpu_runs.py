@@ -49,11 +49,18 @@ def test_workload1_final_kl_within_one_percent():
     assert abs(kl_gpu - kl_orc) <= 0.01 * kl_orc
 
 
-def test_full_size_gradient():
-    N, s = 1_000_000, 2
-    args = inputs.mixture_args(3, job=0, N=N)
+@pytest.fixture(scope="module")
+def p1m():
+    """P of the benchmark's workload (N = 1M, 100 clusters + 5% background)."""
+    args = inputs.mixture_args(3, job=0, N=1_000_000)
     P = inputs.affinities(inputs.mixture(**args), 30.0, device="cuda")
     torch.cuda.empty_cache()
+    return P, args
+
+
+def test_full_size_gradient(p1m):
+    N, s = 1_000_000, 2
+    P, args = p1m
     rng = np.random.default_rng(2024)
     c = rng.normal(0, 25.0, size=(100, s))
     lab = rng.integers(0, 100, size=N)
@@ -96,3 +103,24 @@ def test_error_against_exact_gradient(s):
     zerr = abs(Z.item() - ex["Z"]) / ex["Z"]
     print(f"s={s} N={N} n_int={info['n_int']}: dY rel L2 vs exact {err:.3e}, Z rel {zerr:.3e}")
     assert err < 0.05 and zerr < 1e-2
+
+
+def test_full_size_force_schedules_agree(p1m):
+    """The benchmark's run up to 20 iterations past the first relabelling under
+    both force-kernel schedules (grid-stride chunks, SM-local regions): Y bit
+    for bit equal."""
+    P, args = p1m
+    N, s = 1_000_000, 2
+    Y0 = inputs.initial_embedding(N, s, seed=args["seed"])
+    sched = pkg.Schedule(n_iter=1000, late_iters=250, late_alpha=4.0)
+    Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+    out = []
+    for mode in (pkg._abi.TSNE_FORCE_GRID, pkg._abi.TSNE_FORCE_REGION):
+        with pkg.Plan(N, s, force_mode=mode) as plan:
+            Y = torch.as_tensor(Y0.copy(), device="cuda")
+            plan.run_reset()
+            plan.run_iters(Pd, Y, sched, 0, 120)
+            torch.cuda.synchronize()
+            assert plan.status() == 0
+            out.append(Y.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
