@@ -274,19 +274,34 @@ def run_batched_compare(n_jobs: int, n_iter: int):
         pl.close()
     del plans, Ys
     torch.cuda.empty_cache()
-    with pkg.Batch(2, max_jobs=max(64, n_jobs)) as b:
-        ids = [b.add(Pd, torch.as_tensor(Y0, device="cuda"), sched) for Pd, (_, Y0) in zip(Pds, jobs)]
-        tuning = b.autotune(iters=3)  # restores every job's state afterwards
-        b.poll()
-        l0 = b.launch_count()
-        t0 = time.perf_counter()
-        b.iterate(n_iter)
-        it, st = b.poll()
-        t_bat = time.perf_counter() - t0
-        launches_bat = b.launch_count() - l0
-        assert all(it[j] == n_iter and st[j] == 0 for j in ids)
-        kl_bat = [b.kl(j) for j in ids]
+    def batched_run(tuning):
+        with pkg.Batch(2, max_jobs=max(64, n_jobs)) as b:
+            ids = [b.add(Pd, torch.as_tensor(Y0, device="cuda"), sched) for Pd, (_, Y0) in zip(Pds, jobs)]
+            if tuning is None:
+                tuning = b.autotune(iters=3)  # restores every job's state afterwards
+                picked = tuning
+            else:
+                b.set_tuning(tuning)
+                picked = None
+            b.poll()
+            l0 = b.launch_count()
+            t0 = time.perf_counter()
+            b.iterate(n_iter)
+            it, st = b.poll()
+            dt = time.perf_counter() - t0
+            launches = b.launch_count() - l0
+            assert all(it[j] == n_iter and st[j] == 0 for j in ids)
+            kls = [b.kl(j) for j in ids]
+        return dt, kls, launches, picked
+
+    # the autotuner's pick (chunk, FFT threads, interval policy), timed
+    t_tuned, kl_tuned, _, tuning = batched_run(None)
+    # the same chunk and FFT threads with the plans' interval rule: the batch then
+    # computes exactly what the loop of plans computes (equal KL, bit for bit)
+    same = pkg.Tuning(tuning.chunk, tuning.fft_threads, pkg._abi.TSNE_NINT_RULE)
+    t_bat, kl_bat, launches_bat, _ = batched_run(same)
     rel = [abs(x - y) / abs(y) for x, y in zip(kl_bat, kl_seq)]
+    rel_tuned = [abs(x - y) / abs(y) for x, y in zip(kl_tuned, kl_seq)]
     sumN = int(sum(P.N for P, _ in jobs))
     return {
         "jobs": n_jobs, "sum_N": sumN, "iterations": n_iter, "s": 2,
@@ -296,13 +311,18 @@ def run_batched_compare(n_jobs: int, n_iter: int):
         "point_iterations_per_s": sumN * n_iter / t_bat,
         "kl_max_rel_diff": max(rel), "kl_mean": float(np.mean(kl_bat)),
         "tuning": {"chunk": tuning.chunk, "fft_threads": tuning.fft_threads,
-                   "n_int_policy": "fill" if tuning.n_int_policy == 1 else "rule",
+                   "n_int_policy": "rule", "autotuner_policy": "fill" if tuning.n_int_policy == 1 else "rule",
                    "ms_per_iter": tuning.ms_per_iter},
+        "autotuned_run": {"embeddings_per_s": n_jobs / t_tuned, "kl_max_rel_diff": max(rel_tuned),
+                          "kl_mean_rel_diff": float(np.mean(rel_tuned)),
+                          "note": "the tuner's own pick; with the fill policy a job uses more "
+                                  "intervals (same FFT length) than the plans' rule, so its "
+                                  "trajectory differs"},
         "gpu_launches_batched": launches_bat, "gpu_launches_sequential": launches_seq,
         "timing": "wall clock around the whole runs, device synchronised",
         "workload": "N log-uniform in [1k, 200k], 10-30-cluster Gaussian mixtures in 50-d, "
-                    "perplexity 30, k=90; one batch (graph per iteration, autotuned) vs a "
-                    "loop of plans",
+                    "perplexity 30, k=90; one batch (graph per iteration, autotuned chunk and FFT "
+                    "threads, the plans' interval rule) vs a loop of plans",
     }
 
 
