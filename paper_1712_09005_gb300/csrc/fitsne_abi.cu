@@ -384,8 +384,8 @@ int enqueue_forces(tsne_plan* pl, int step) {
     if (pl->force_mode == TSNE_FORCE_GRID) {
         CU(fitsne::launch_forces(pl->d_job, pl->caps, step, pl->stream), "force kernel launch");
     } else {
-        CU(fitsne::launch_forces_region(pl->d_job, pl->s, pl->p, step, pl->region_next,
-                                        pl->n_regions, pl->sm_count, pl->stream),
+        CU(fitsne::launch_forces_region(pl->d_job, pl->caps, step, pl->region_next,
+                                        pl->n_regions, pl->stream),
            "force kernel launch");
     }
     pl->launches += 1;

@@ -60,6 +60,8 @@ struct tsne_batch {
     double* kl_partial;
     unsigned* kl_ticket;
     double* kl_out;
+    unsigned* region_next;  // [n_regions + 1] counters of the SM-local force schedule
+    int n_regions;
     int64_t launches;
     int64_t bytes_in_use;
 };
@@ -170,7 +172,8 @@ int enqueue_iteration(tsne_batch* b) {
     CU(fitsne::launch_box(b->d_table, c, b->tables, 0, b->stream), "box launch");
     CU(fitsne::launch_sort_and_spread(b->d_table, c, b->stream), "sort/spread launch");
     CU(fitsne::launch_convolution(b->d_table, c, b->tables, b->stream), "FFT launch");
-    CU(fitsne::launch_forces(b->d_table, c, 1, b->stream), "force launch");
+    CU(fitsne::launch_forces_region(b->d_table, c, 1, b->region_next, b->n_regions, b->stream),
+       "force launch");
     CU(fitsne::launch_advance(b->d_table, c.njobs, b->stream), "advance launch");
     return TSNE_OK;
 }
@@ -315,6 +318,7 @@ int tsne_batch_create(int32_t s, int32_t p, const tsne_batch_opts* opts, tsne_ba
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->kl_partial, sizeof(double) * 2 * 4 * b->sm_count);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->kl_ticket, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->kl_out, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->region_next, sizeof(unsigned) * 1024);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_table, sizeof(Job) * max_jobs);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_dyn, sizeof(JobDyn) * max_jobs);
     if (e != cudaSuccess) {
@@ -333,6 +337,14 @@ int tsne_batch_create(int32_t s, int32_t p, const tsne_batch_opts* opts, tsne_ba
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_dyn, 0, sizeof(JobDyn) * max_jobs, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->kl_ticket, 0, sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = fitsne::fft_configure(s, b->fft.L_max);
+    if (e == cudaSuccess) {
+        // the SM id range sizes the SM-local force schedule
+        int* d = reinterpret_cast<int*>(b->region_next);
+        e = fitsne::query_sm_id_count(d, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&b->n_regions, d, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e == cudaSuccess && (b->n_regions < 1 || b->n_regions > 1023)) b->n_regions = b->sm_count;
+    }
     if (e == cudaSuccess) e = cudaEventRecord(b->table_ev, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return fail_free(cuda_fail(e, "batch initialisation"));
@@ -347,7 +359,8 @@ int tsne_batch_destroy(tsne_batch* b) {
     for (Slot& S : b->slots)
         if (S.mem) cudaFree(S.mem);
     fitsne::fft_set_destroy(&b->fft);
-    void* dev[] = {b->d_table, b->d_dyn, b->d_fill_table, b->kl_partial, b->kl_ticket, b->kl_out};
+    void* dev[] = {b->d_table, b->d_dyn, b->d_fill_table, b->kl_partial, b->kl_ticket, b->kl_out,
+                   b->region_next};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (b->h_table) cudaFreeHost(b->h_table);

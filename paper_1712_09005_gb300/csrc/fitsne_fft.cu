@@ -205,32 +205,59 @@ __device__ __forceinline__ int fft_1d_items(const Job& J) {
 }  // namespace
 
 // ----------------------------------------------------------------------------
-// 2-D, pass 1: row FFTs. Work item m < 4n of a job: type m / n (0: C0, 1: C1,
+// Rows per work item of a row pass: as many rows of length L as the launch's
+// shared memory holds (per_row float2 each), but no more than keeps about
+// 4 items per SM over the whole table.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int rows_per_item(int L, int per_row, int smem_floats2, int total_rows,
+                                             int sm_count) {
+    int rp = smem_floats2 / (per_row * L);
+    int want = total_rows / (4 * sm_count);
+    if (want < 1) want = 1;
+    if (rp > want) rp = want;
+    if (rp > 16) rp = 16;
+    return rp < 1 ? 1 : rp;
+}
+
+// ----------------------------------------------------------------------------
+// 2-D, pass 1: row FFTs. Row m < 4n of a job: type m / n (0: C0, 1: C1,
 // 2: CK, 3: CG), row r = m % n (for CK and CG the offset o1 = r >= 0). Output
-// rows of length L, row-major, at spec + type n L.
+// rows of length L, row-major, at spec + type n L. A work item takes rp
+// consecutive rows (one batched FFT).
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-rows_fwd_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
+rows_fwd_kernel(const Job* __restrict__ jobs, int njobs, Tables tab, int smem_floats2,
+                int sm_count) {
     extern __shared__ float2 sm[];
     __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ FftEntry e;
-    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_rows_items(J); });
+    const int total_rows = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_rows_items(J); });
+    const int total = split_jobs(jobs, njobs, s_start, [&](const Job& J) {
+        const int rows = fft_rows_items(J);
+        if (!rows) return 0;
+        const int rp = rows_per_item(J.params->L, 2, smem_floats2, total_rows, sm_count);
+        return (rows + rp - 1) / rp;
+    });
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int j = job_of(s_start, njobs, item);
         const Job& J = jobs[j];
-        const int m = item - s_start[j];
         const Params P = *J.params;
         if (threadIdx.x == 0) e = tab.fft[P.fft_idx];
         __syncthreads();
         const int n = P.n, L = P.L;
+        const int rpj = rows_per_item(L, 2, smem_floats2, total_rows, sm_count);
+        const int m0 = (item - s_start[j]) * rpj;
+        const int rp = min(rpj, 4 * n - m0);
         const int64_t G = (int64_t)n * n;
         const long long* __restrict__ w = J.w;
         const float2* tw = tab.tw + e.tw_off;
         const float inv = P.fx_inv;
         float2* A = sm;
-        float2* B = sm + L;
-        const int type = m / n, r = m - type * n;
-        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+        float2* B = sm + rp * L;
+        for (int idx = threadIdx.x; idx < rp * L; idx += blockDim.x) {
+            const int q = idx / L, c = idx - q * L;
+            const int m = m0 + q;
+            const int type = m / n, r = m - type * n;
             float2 v = make_float2(0.0f, 0.0f);
             if (type == 0) {
                 if (c < n) v = make_float2(fx(w[(int64_t)r * n + c], inv), fx(w[G + (int64_t)r * n + c], inv));
@@ -248,14 +275,24 @@ rows_fwd_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
                     }
                 }
             }
-            A[c] = v;
+            A[idx] = v;
         }
         __syncthreads();
-        const float2* res = fft_batch(A, B, e, 1, tw, -1.0f);
-        float2* dst = J.spec + (int64_t)type * n * L + (int64_t)r * L;
-        for (int c = threadIdx.x; c < L; c += blockDim.x) dst[c] = res[c];
+        const float2* res = fft_batch(A, B, e, rp, tw, -1.0f);
+        for (int idx = threadIdx.x; idx < rp * L; idx += blockDim.x) {
+            const int q = idx / L, c = idx - q * L;
+            const int m = m0 + q;
+            const int type = m / n, r = m - type * n;
+            J.spec[(int64_t)type * n * L + (int64_t)r * L + c] = res[idx];
+        }
         __syncthreads();
     }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // Block sum of one double per thread (blockDim.x <= 1024); result in thread 0.
@@ -282,46 +319,76 @@ __device__ void publish_Z(double S, const Job& J) {
 
 // ----------------------------------------------------------------------------
 // 2-D, pass 2: column pairs (k2, L - k2), k2 = 0 .. L/2 of a job. Forward FFT
-// of six columns (C0 and C1 at k2 and L - k2, CK and CG at k2), spectra
-// products, inverse FFT of the four packed results, which overwrite the first
-// n rows of columns k2 and L - k2 of C0 and C1. The last item of a job sums
-// the Parseval terms into Z.
+// of six columns per pair (C0 and C1 at k2 and L - k2, CK and CG at k2),
+// spectra products, inverse FFT of the four packed results, which overwrite
+// the first n rows of columns k2 and L - k2 of C0 and C1.
+// A work item takes cp adjacent pairs: its loads and stores of a row then
+// touch cp consecutive values (whole sectors rather than one value in four),
+// and each FFT stage has 6 cp transforms' butterflies for the CTA's threads.
+// cp is as large as the launch's shared memory allows for the job's L, and
+// no larger than keeps about 4 items per SM over the whole table (a lone
+// small grid keeps one pair per item).
+// Each pair's Parseval terms of Z are summed in an order fixed by L alone
+// (lane l of one warp adds k1 = l, l + 32, ...; then an xor tree), so Z does
+// not depend on cp or on the CTA size; the last item of a job adds the pairs'
+// sums in pair order.
 // Rows o1 < 0 of the kernels: CK row -r = CK row r (even); the CG row
 // spectrum is real with X_{-r}[k2] = -X_r[L - k2] (G_1 odd, G_2 even in o1).
 // At column L - k2 the kernel spectra are K^(k1, k2), S_1(k1, k2) and
 // -S_2(k1, k2) (G_2 is odd in o2).
 // ----------------------------------------------------------------------------
+__device__ __forceinline__ int cols_per_item(int L, int smem_floats2, int total_pairs, int sm_count) {
+    int cp = smem_floats2 / (12 * L);
+    int want = total_pairs / (4 * sm_count);
+    if (want < 1) want = 1;
+    if (cp > want) cp = want;
+    if (cp > 8) cp = 8;
+    return cp < 1 ? 1 : cp;
+}
+
 __global__ void __launch_bounds__(1024)
-cols_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
+cols_kernel(const Job* __restrict__ jobs, int njobs, Tables tab, int smem_floats2, int sm_count) {
     extern __shared__ float2 sm[];
     __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ FftEntry e;
-    __shared__ double sred[32];
     __shared__ bool s_last;
-    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_cols_items(J); });
+    // column pairs of the whole table, then items per job
+    const int total_pairs = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_cols_items(J); });
+    const int total = split_jobs(jobs, njobs, s_start, [&](const Job& J) {
+        const int pairs = fft_cols_items(J);
+        if (!pairs) return 0;
+        const int cp = cols_per_item(J.params->L, smem_floats2, total_pairs, sm_count);
+        return (pairs + cp - 1) / cp;
+    });
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32, nwarps = blockDim.x / 32;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int j = job_of(s_start, njobs, item);
         const Job& J = jobs[j];
-        const int k2 = item - s_start[j], nk = s_start[j + 1] - s_start[j];
+        const int it = item - s_start[j], nk = s_start[j + 1] - s_start[j];
         const Params P = *J.params;
         if (threadIdx.x == 0) e = tab.fft[P.fft_idx];
         __syncthreads();
         const int n = P.n, L = P.L;
+        const int cpj = cols_per_item(L, smem_floats2, total_pairs, sm_count);
+        const int k2_0 = it * cpj;
+        const int cp = min(cpj, L / 2 + 1 - k2_0);
         const float2* tw = tab.tw + e.tw_off;
         float2* C0 = J.spec;
         float2* C1 = J.spec + (int64_t)n * L;
         const float2* CK = J.spec + 2 * (int64_t)n * L;
         const float2* CG = J.spec + 3 * (int64_t)n * L;
         float2* X = sm;
-        float2* Yb = sm + 6 * L;
+        float2* Yb = sm + 6 * cp * L;
         const float2 z = make_float2(0.0f, 0.0f);
-        const int k2b = (L - k2) % L;
-        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        for (int idx = threadIdx.x; idx < L * cp; idx += blockDim.x) {
+            const int i = idx / cp, pq = idx - i * cp;
+            const int k2 = k2_0 + pq, k2b = (L - k2) % L;
+            float2* Xp = X + 6 * pq * L;
             const bool in = i < n;
-            X[i] = in ? C0[(int64_t)i * L + k2] : z;
-            X[L + i] = in ? C0[(int64_t)i * L + k2b] : z;
-            X[2 * L + i] = in ? C1[(int64_t)i * L + k2] : z;
-            X[3 * L + i] = in ? C1[(int64_t)i * L + k2b] : z;
+            Xp[i] = in ? C0[(int64_t)i * L + k2] : z;
+            Xp[L + i] = in ? C0[(int64_t)i * L + k2b] : z;
+            Xp[2 * L + i] = in ? C1[(int64_t)i * L + k2] : z;
+            Xp[3 * L + i] = in ? C1[(int64_t)i * L + k2b] : z;
             float2 ck = z, cg = z;
             if (in) {
                 ck = CK[(int64_t)i * L + k2];
@@ -331,17 +398,21 @@ cols_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
                 const float2 t = CG[(int64_t)(L - i) * L + k2b];
                 cg = make_float2(-t.x, -t.y);
             }
-            X[4 * L + i] = ck;
-            X[5 * L + i] = cg;
+            Xp[4 * L + i] = ck;
+            Xp[5 * L + i] = cg;
         }
         __syncthreads();
-        float2* F = fft_batch(X, Yb, e, 6, tw, -1.0f);
+        float2* F = fft_batch(X, Yb, e, 6 * cp, tw, -1.0f);
         float2* O = (F == X) ? Yb : X;
-        double zp = 0.0;
-        for (int k1 = threadIdx.x; k1 < L; k1 += blockDim.x) {
+        double* zt = reinterpret_cast<double*>(O + 4 * cp * L);  // the buffer's unused tail
+        for (int idx = threadIdx.x; idx < L * cp; idx += blockDim.x) {
+            const int pq = idx / L, k1 = idx - pq * L;
+            const int k2 = k2_0 + pq, k2b = (L - k2) % L;
+            const float2* Fp = F + 6 * pq * L;
+            float2* Op = O + 4 * pq * L;
             const int k1n = (L - k1) % L;
-            const float2 xa = F[k1], xb = F[L + k1];
-            const float2 xa_m = F[k1n], xb_m = F[L + k1n];
+            const float2 xa = Fp[k1], xb = Fp[L + k1];
+            const float2 xa_m = Fp[k1n], xb_m = Fp[L + k1n];
             // C0 = w0 + i d_1 split at (k1, k2) [a] and (k1, L - k2) [b]
             const float2 w0a = cscale(cadd(xa, conjf2(xb_m)), 0.5f);
             const float2 ta = csub(xa, conjf2(xb_m));
@@ -349,12 +420,12 @@ cols_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
             const float2 w0b = cscale(cadd(xb, conjf2(xa_m)), 0.5f);
             const float2 tb = csub(xb, conjf2(xa_m));
             const float2 d1b = make_float2(0.5f * tb.y, -0.5f * tb.x);
-            const float2 d2a = F[2 * L + k1], d2b = F[3 * L + k1];
-            const float2 ck = F[4 * L + k1];      // (K1^, K2^)
-            const float2 cg = F[5 * L + k1];      // i S1 - S2
+            const float2 d2a = Fp[2 * L + k1], d2b = Fp[3 * L + k1];
+            const float2 ck = Fp[4 * L + k1];      // (K1^, K2^)
+            const float2 cg = Fp[5 * L + k1];      // i S1 - S2
             const float K1 = ck.x, K2 = ck.y, S1 = cg.y, S2 = -cg.x;
             // Parseval terms of Z + N at (k1, k2) and (k1, L - k2)
-            zp += ((double)w0a.x * w0a.x + (double)w0a.y * w0a.y) * (double)K1;
+            double zp = ((double)w0a.x * w0a.x + (double)w0a.y * w0a.y) * (double)K1;
             if (k2b != k2) zp += ((double)w0b.x * w0b.x + (double)w0b.y * w0b.y) * (double)K1;
             // U1 = d1 K2 - i S1 w0, U2 = d2 K2 - i S2 w0, V = w0 K2 (S2 flips sign at L - k2)
             const float2 va = cscale(w0a, K2), vb = cscale(w0b, K2);
@@ -362,21 +433,30 @@ cols_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
             const float2 u2a = csub(cscale(d2a, K2), mul_si(w0a, S2));
             const float2 u1b = csub(cscale(d1b, K2), mul_si(w0b, S1));
             const float2 u2b = cadd(cscale(d2b, K2), mul_si(w0b, S2));
-            O[k1] = cadd(u1a, mul_si(u2a, 1.0f));
-            O[L + k1] = cadd(u1b, mul_si(u2b, 1.0f));
-            O[2 * L + k1] = va;
-            O[3 * L + k1] = vb;
+            Op[k1] = cadd(u1a, mul_si(u2a, 1.0f));
+            Op[L + k1] = cadd(u1b, mul_si(u2b, 1.0f));
+            Op[2 * L + k1] = va;
+            Op[3 * L + k1] = vb;
+            zt[pq * L + k1] = zp;
         }
-        const double zt = block_sum_d(zp, sred);
-        if (threadIdx.x == 0) J.z_partial[k2] = zt;
         __syncthreads();
-        const float2* R = fft_batch(O, F, e, 4, tw, 1.0f);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            C0[(int64_t)i * L + k2] = R[i];
-            C1[(int64_t)i * L + k2] = R[2 * L + i];
+        for (int pq = wid; pq < cp; pq += nwarps) {
+            double zs = 0.0;
+            for (int k1 = lane; k1 < L; k1 += 32) zs += zt[pq * L + k1];
+            zs = warp_sum_d(zs);
+            if (lane == 0) J.z_partial[k2_0 + pq] = zs;
+        }
+        __syncthreads();
+        const float2* R = fft_batch(O, F, e, 4 * cp, tw, 1.0f);
+        for (int idx = threadIdx.x; idx < n * cp; idx += blockDim.x) {
+            const int i = idx / cp, pq = idx - i * cp;
+            const int k2 = k2_0 + pq, k2b = (L - k2) % L;
+            const float2* Rp = R + 4 * pq * L;
+            C0[(int64_t)i * L + k2] = Rp[i];
+            C1[(int64_t)i * L + k2] = Rp[2 * L + i];
             if (k2b != k2) {
-                C0[(int64_t)i * L + k2b] = R[L + i];
-                C1[(int64_t)i * L + k2b] = R[3 * L + i];
+                C0[(int64_t)i * L + k2b] = Rp[L + i];
+                C1[(int64_t)i * L + k2b] = Rp[3 * L + i];
             }
         }
         if (threadIdx.x == 0) {
@@ -397,38 +477,50 @@ cols_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
 
 // ----------------------------------------------------------------------------
 // 2-D, pass 3: inverse row FFTs of the first n rows of D0 and D1; node
-// values (0, u'_1, u'_2, v) / L^2 for columns < n.
+// values (0, u'_1, u'_2, v) / L^2 for columns < n. A work item takes rp
+// consecutive rows (2 rp transforms in one batch).
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-rows_inv_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
+rows_inv_kernel(const Job* __restrict__ jobs, int njobs, Tables tab, int smem_floats2,
+                int sm_count) {
     extern __shared__ float2 sm[];
     __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ FftEntry e;
-    const int total = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_inv_items(J); });
+    const int total_rows = split_jobs(jobs, njobs, s_start, [](const Job& J) { return fft_inv_items(J); });
+    const int total = split_jobs(jobs, njobs, s_start, [&](const Job& J) {
+        const int rows = fft_inv_items(J);
+        if (!rows) return 0;
+        const int rp = rows_per_item(J.params->L, 4, smem_floats2, total_rows, sm_count);
+        return (rows + rp - 1) / rp;
+    });
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int j = job_of(s_start, njobs, item);
         const Job& J = jobs[j];
-        const int r = item - s_start[j];
         const Params P = *J.params;
         if (threadIdx.x == 0) e = tab.fft[P.fft_idx];
         __syncthreads();
         const int n = P.n, L = P.L;
+        const int rpj = rows_per_item(L, 4, smem_floats2, total_rows, sm_count);
+        const int r0 = (item - s_start[j]) * rpj;
+        const int rp = min(rpj, n - r0);
         const float2* tw = tab.tw + e.tw_off;
         const float2* D0 = J.spec;
         const float2* D1 = J.spec + (int64_t)n * L;
         float4* __restrict__ hgrid = J.hgrid;
         float2* X = sm;
-        float2* Yb = sm + 2 * L;
+        float2* Yb = sm + 2 * rp * L;
         const float scale = 1.0f / ((float)L * (float)L);
-        for (int c = threadIdx.x; c < L; c += blockDim.x) {
-            X[c] = D0[(int64_t)r * L + c];
-            X[L + c] = D1[(int64_t)r * L + c];
+        for (int idx = threadIdx.x; idx < rp * L; idx += blockDim.x) {
+            const int q = idx / L, c = idx - q * L;
+            X[2 * q * L + c] = D0[(int64_t)(r0 + q) * L + c];
+            X[(2 * q + 1) * L + c] = D1[(int64_t)(r0 + q) * L + c];
         }
         __syncthreads();
-        const float2* R = fft_batch(X, Yb, e, 2, tw, 1.0f);
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            const float2 a = R[c], b = R[L + c];
-            hgrid[(int64_t)r * n + c] = make_float4(0.0f, a.x * scale, a.y * scale, b.x * scale);
+        const float2* R = fft_batch(X, Yb, e, 2 * rp, tw, 1.0f);
+        for (int idx = threadIdx.x; idx < rp * n; idx += blockDim.x) {
+            const int q = idx / n, c = idx - q * n;
+            const float2 a = R[2 * q * L + c], b = R[(2 * q + 1) * L + c];
+            hgrid[(int64_t)(r0 + q) * n + c] = make_float4(0.0f, a.x * scale, a.y * scale, b.x * scale);
         }
         __syncthreads();
     }
@@ -515,9 +607,9 @@ conv1d_kernel(const Job* __restrict__ jobs, int njobs, Tables tab) {
 // sequence (or a captured graph of it) serves every iteration whatever N_int
 // the box rule picks.
 // ----------------------------------------------------------------------------
-static size_t smem_rows_fwd(int L_max) { return sizeof(float2) * 2 * L_max; }
+static size_t smem_rows_fwd(int L_max) { return sizeof(float2) * std::max(2 * L_max, 8192); }
 static size_t smem_cols(int L_max) { return sizeof(float2) * 12 * L_max; }
-static size_t smem_rows_inv(int L_max) { return sizeof(float2) * 4 * L_max; }
+static size_t smem_rows_inv(int L_max) { return sizeof(float2) * std::max(4 * L_max, 8192); }
 static size_t smem_1d(int L_max) { return sizeof(float2) * 4 * L_max; }
 
 cudaError_t fft_configure(int s, int L_max) {
@@ -550,11 +642,17 @@ cudaError_t launch_convolution(const Job* jobs, const TableCaps& c, const Tables
         const int tr = c.fft_threads > 0 ? c.fft_threads : 256;
         const int tc = c.fft_threads > 0 ? c.fft_threads : 512;
         const int g1 = cap_grid(4 * (int64_t)c.max_n * J, 4LL * c.sm_count);
-        rows_fwd_kernel<<<g1, tr, smem_rows_fwd(c.max_L), st>>>(jobs, c.njobs, t);
+        // a lone job's grid already gives more rows than SMs: one row per item, and
+        // the smaller shared-memory request keeps more CTAs resident
+        const size_t sf = c.njobs > 1 ? smem_rows_fwd(c.max_L) : sizeof(float2) * 2 * c.max_L;
+        rows_fwd_kernel<<<g1, tr, sf, st>>>(jobs, c.njobs, t, (int)(sf / sizeof(float2)), c.sm_count);
         const int g2 = cap_grid((int64_t)(c.max_L / 2 + 1) * J, 2LL * c.sm_count);
-        cols_kernel<<<g2, tc, smem_cols(c.max_L), st>>>(jobs, c.njobs, t);
+        cols_kernel<<<g2, tc, smem_cols(c.max_L), st>>>(jobs, c.njobs, t,
+                                                       (int)(smem_cols(c.max_L) / sizeof(float2)),
+                                                       c.sm_count);
         const int g3 = cap_grid((int64_t)c.max_n * J, 4LL * c.sm_count);
-        rows_inv_kernel<<<g3, tr, smem_rows_inv(c.max_L), st>>>(jobs, c.njobs, t);
+        const size_t si = c.njobs > 1 ? smem_rows_inv(c.max_L) : sizeof(float2) * 4 * c.max_L;
+        rows_inv_kernel<<<g3, tr, si, st>>>(jobs, c.njobs, t, (int)(si / sizeof(float2)), c.sm_count);
     } else {
         const int g = cap_grid(J, c.sm_count);
         conv1d_kernel<<<g, 1024, smem_1d(c.max_L), st>>>(jobs, c.njobs, t);

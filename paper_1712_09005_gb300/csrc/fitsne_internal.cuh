@@ -379,10 +379,10 @@ cudaError_t launch_convolution(const Job* jobs, const TableCaps& c, const Tables
                                cudaStream_t st);
 cudaError_t launch_forces(const Job* jobs, const TableCaps& c, int step, cudaStream_t st);
 cudaError_t launch_advance(const Job* jobs, int njobs, cudaStream_t st);
-// Force/update step of one job with SM-local scheduling of its 32-row blocks
+// Force/update step with SM-local scheduling of the tables' 32-row blocks
 // (next: n_regions counters and the claimed total, zeroed here before the launch).
-cudaError_t launch_forces_region(const Job* jobs, int s, int p, int step, unsigned* next,
-                                 int n_regions, int sm_count, cudaStream_t st);
+cudaError_t launch_forces_region(const Job* jobs, const TableCaps& c, int step, unsigned* next,
+                                 int n_regions, cudaStream_t st);
 // Writes the device's SM id range (%nsmid) to out_dev.
 cudaError_t query_sm_id_count(int* out_dev, cudaStream_t st);
 // Stream-ordered write of one table row (and, if dyn is not NULL, its JobDyn)

@@ -933,39 +933,41 @@ __device__ __forceinline__ unsigned sm_id_count() {
     return r;
 }
 
-// The step (or gradient) of one job with SM-local work: the 32-row blocks
-// are cut into n_regions contiguous regions (n_regions >= the SM id range);
-// the warps resident on the SM with id r take the blocks of region r, in
-// order, through the region's counter next[r]. Rows of a relabelled run that
-// are close in label are close in the embedding and share most neighbours,
-// so all warps of an SM gather from one working set of y_j that the SM's L1
-// holds. A warp whose own region is used up moves on to regions r + 1, r + 2,
-// ... (cyclically) to help SMs that are behind, and stops as soon as the
-// count of claimed blocks (next[n_regions]) reaches the total, so the tail
-// costs no more than the last claims. The loop ends: every probe either
-// claims a block (finitely many) or moves to the next region (at most
-// n_regions moves). next[0 .. n_regions] must be zero at launch.
+// The step (or gradient) with SM-local work. The 32-row blocks of all jobs
+// of the table (job after job) are cut into n_regions contiguous regions
+// (n_regions >= the SM id range); the warps resident on the SM with id r take
+// the blocks of region r, in order, through the region's counter next[r].
+// So the warps of an SM work on one contiguous range of rows: in a relabelled
+// run these are close in the embedding and share most neighbours, and in a
+// batch of small jobs they belong to one job; either way the y_j they gather
+// form one working set that the SM's L1 holds. A warp whose own region is
+// used up moves on to regions r + 1, r + 2, ... (cyclically) to help SMs that
+// are behind, and stops as soon as the count of claimed blocks
+// (next[n_regions]) reaches the total, so the tail costs no more than the
+// last claims. The loop ends: every probe either claims a block (finitely
+// many) or moves to the next region (at most n_regions moves).
+// next[0 .. n_regions] must be zero at launch.
 template <int S, int PP, bool STEP>
 __global__ void __launch_bounds__(256, FITSNE_FORCE_MINB)
-force_region_kernel(const Job* __restrict__ jobs, unsigned* __restrict__ next, int n_regions) {
-    const Job& J = jobs[0];
-    const Params* __restrict__ Pp = J.params;
-    if (!job_live(*Pp)) return;
-    const int64_t N = J.N;
-    const float* __restrict__ Y = J.ybuf[Pp->cur];
+force_region_kernel(const Job* __restrict__ jobs, int njobs, unsigned* __restrict__ next,
+                    int n_regions) {
+    __shared__ int32_t s_start[kMaxJobs + 1];
+    const int nblk = split_jobs(jobs, njobs, s_start, [](const Job& J) {
+        const Params* P = J.params;
+        return job_live(*P) ? (int)((J.N + 31) / 32) : 0;
+    });
     const int lane = threadIdx.x % 32;
-    const int64_t nblk = (N + 31) / 32;
     const int home = (int)(sm_id() % (unsigned)n_regions);
     unsigned* claimed = next + n_regions;
     for (int hop = 0; hop < n_regions;) {
         const int r = (home + hop) % n_regions;
-        const int64_t b0 = nblk * r / n_regions, b1 = nblk * (r + 1) / n_regions;
-        int64_t blk = -1;
+        const int b0 = (int)((int64_t)nblk * r / n_regions), b1 = (int)((int64_t)nblk * (r + 1) / n_regions);
+        int blk = -1;
         if (lane == 0) {
             if (hop == 0 || *(volatile unsigned*)claimed < (unsigned)nblk) {
                 const unsigned k = atomicAdd(&next[r], 1u);
                 if (b0 + (int64_t)k < b1) {
-                    blk = b0 + k;
+                    blk = b0 + (int)k;
                     atomicAdd(claimed, 1u);
                 }
             } else {
@@ -975,7 +977,11 @@ force_region_kernel(const Job* __restrict__ jobs, unsigned* __restrict__ next, i
         blk = __shfl_sync(kFull, blk, 0);
         if (blk == -2) break;
         if (blk < 0) { ++hop; continue; }
-        force_block<S, PP, STEP>(J, Pp, Y, blk * 32, N, lane);
+        const int jb = job_of(s_start, njobs, blk);
+        const Job& J = jobs[jb];
+        const Params* __restrict__ Pp = J.params;
+        const float* __restrict__ Y = J.ybuf[Pp->cur];
+        force_block<S, PP, STEP>(J, Pp, Y, (int64_t)(blk - s_start[jb]) * 32, J.N, lane);
     }
 }
 
@@ -1138,20 +1144,19 @@ static void forces_impl(const Job* jobs, const TableCaps& c, int step, cudaStrea
 }
 
 template <int S, int PP>
-static void region_impl(const Job* jobs, int step, unsigned* next, int n_regions, int sm_count,
-                        cudaStream_t st) {
+static void region_impl(const Job* jobs, int njobs, int step, unsigned* next, int n_regions,
+                        int sm_count, cudaStream_t st) {
     const int g = FITSNE_FORCE_MINB * sm_count;
-    if (step) force_region_kernel<S, PP, true><<<g, 256, 0, st>>>(jobs, next, n_regions);
-    else force_region_kernel<S, PP, false><<<g, 256, 0, st>>>(jobs, next, n_regions);
+    if (step) force_region_kernel<S, PP, true><<<g, 256, 0, st>>>(jobs, njobs, next, n_regions);
+    else force_region_kernel<S, PP, false><<<g, 256, 0, st>>>(jobs, njobs, next, n_regions);
 }
 
-cudaError_t launch_forces_region(const Job* jobs, int s, int p, int step, unsigned* next,
-                                 int n_regions, int sm_count, cudaStream_t st) {
+cudaError_t launch_forces_region(const Job* jobs, const TableCaps& c, int step, unsigned* next,
+                                 int n_regions, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned) * (n_regions + 1), st);
     if (e != cudaSuccess) return e;
-    const TableCaps c{s, p};
-    if (s == 2) { FITSNE_DISPATCH(2, region_impl, jobs, step, next, n_regions, sm_count, st); }
-    else { FITSNE_DISPATCH(1, region_impl, jobs, step, next, n_regions, sm_count, st); }
+    if (c.s == 2) { FITSNE_DISPATCH(2, region_impl, jobs, c.njobs, step, next, n_regions, c.sm_count, st); }
+    else { FITSNE_DISPATCH(1, region_impl, jobs, c.njobs, step, next, n_regions, c.sm_count, st); }
     return cudaGetLastError();
 }
 

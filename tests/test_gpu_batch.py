@@ -219,3 +219,25 @@ def test_batch_kl_and_capacity():
         assert b.bytes_in_use() == b.job_bytes(2503)
         j2 = b.add(Pd, torch.as_tensor(Y0, device="cuda"), sched)
         assert j2 == j1
+
+
+def test_tuning_knobs_do_not_change_results():
+    """The spread's integer sums, the FFT's per-element arithmetic and Z's
+    fixed-order Parseval sum make a job's result independent of the spread
+    work-item size and the FFT passes' CTA size (only the interval policy
+    changes the approximation)."""
+    s = 2
+    sched = pkg.Schedule(n_iter=12)
+    res = []
+    for chunk, thr in ((128, 0), (32, 1024), (256, 256), (64, 512)):
+        with pkg.Batch(s, max_jobs=4) as b:
+            b.set_tuning(pkg.Tuning(chunk, thr, pkg._abi.TSNE_NINT_RULE))
+            js = []
+            for N, seed in SIZES[:3]:
+                P, Y0 = job(N, seed, s)
+                js.append(b.add(pkg.DeviceCSR.from_host(*P.as_tuple()), torch.as_tensor(Y0 * 500.0, device="cuda"), sched))
+            b.iterate(12)
+            res.append([b.get_y(j).cpu().numpy() for j in js])
+    for other in res[1:]:
+        for a, c in zip(res[0], other):
+            assert np.array_equal(a, c)
