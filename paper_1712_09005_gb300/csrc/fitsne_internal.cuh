@@ -277,6 +277,15 @@ __device__ __forceinline__ int warp_incl_scan(int x) {
 template <typename F>
 __device__ __forceinline__ int split_jobs(const Job* __restrict__ jobs, int njobs, int32_t* s_start,
                                           F count) {
+    if (njobs == 1) {  // a plan: one count, two barriers
+        __syncthreads();   // an earlier split's total has been read by every thread
+        if (threadIdx.x == 0) {
+            s_start[0] = 0;
+            s_start[1] = count(jobs[0]);
+        }
+        __syncthreads();
+        return s_start[1];
+    }
     __shared__ int32_t s_wsum[32];
     __shared__ int32_t s_carry;
     const int lane = threadIdx.x % 32, wid = threadIdx.x / 32, nw = blockDim.x / 32;

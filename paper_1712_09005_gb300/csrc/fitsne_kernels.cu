@@ -1118,7 +1118,9 @@ static void sort_and_spread_impl(const Job* jobs, const TableCaps& c, cudaStream
     scan_blocks_kernel<<<gsc, 1024, 0, st>>>(jobs, c.njobs);
     scan_boxes_kernel<<<gsc, 1024, 0, st>>>(jobs, c.njobs);
     scatter_kernel<S><<<gp, 256, hs, st>>>(jobs, c.njobs);
-    const int gs = grid_cap(c.sum_chunk_cap * 32, 256, 8LL * c.sm_count);
+    // one resident wave (the kernel's registers allow two 256-thread CTAs per SM);
+    // warps loop over the chunks
+    const int gs = grid_cap(c.sum_chunk_cap * 32, 256, 2LL * c.sm_count);
     spread_kernel<S, PP><<<gs, 256, 0, st>>>(jobs, c.njobs);
 }
 
