@@ -311,7 +311,7 @@ typedef struct {
 
 /* Tuning of a batch (see tsne_batch_autotune). */
 typedef struct {
-    int32_t chunk;        /* points per spread work item, one warp each: 32, 64, 128 [128] or 256
+    int32_t chunk;        /* points per spread work item, one warp each: 32, 64 [64], 128 or 256
                              (a box of c points gets ceil(c / chunk) warps) */
     int32_t fft_threads;  /* threads per CTA of the 2-D FFT passes: 256, 512, 1024, or 0 [0] for
                              256 (row passes) / 512 (column pass) */

@@ -225,7 +225,7 @@ def tsne_kl_noalloc(P: DeviceCSR, Y: torch.Tensor, s: int, Z: float, kl_out: tor
 @dataclass
 class Tuning:
     """tsne_batch_tuning: spread work item, FFT threads per CTA, interval policy."""
-    chunk: int = 128
+    chunk: int = 64
     fft_threads: int = 0
     n_int_policy: int = _abi.TSNE_NINT_RULE
     ms_per_iter: float = 0.0

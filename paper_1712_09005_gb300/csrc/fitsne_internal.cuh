@@ -29,7 +29,10 @@ constexpr int kSortPts = 2048;    // points per work item of the sort kernels (2
 constexpr int kForceChunk = 256;  // rows per work item of the force kernel (8 warps x 32)
 constexpr int kMaxJobs = 256;     // jobs of one table
 constexpr int kMinChunk = 32;     // smallest spread work item (points)
-constexpr int kDefaultChunk = 128;
+#ifndef FITSNE_DEFAULT_CHUNK
+#define FITSNE_DEFAULT_CHUNK 64
+#endif
+constexpr int kDefaultChunk = FITSNE_DEFAULT_CHUNK;  // points per spread work item of a plan
 
 // One FFT length of the table: L = product of radix[0..nst), each radix in
 // {2, 3, 4, 5}; tw_off locates its L twiddles exp(-2 pi i j / L).
