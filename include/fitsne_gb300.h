@@ -391,6 +391,39 @@ int64_t tsne_batch_launch_count(const tsne_batch* batch);
 void* tsne_batch_stream(const tsne_batch* batch);
 
 /*
+ * Input affinities P from data X on the GPU (Sec. 1.1, Eq. p_ij, with the
+ * k exact nearest neighbours of Sec. 3 in place of all points):
+ *   p_{j|i} = exp(-beta_i d_ij^2) / sum_{l in kNN(i)} exp(-beta_i d_il^2)
+ *   beta_i by bisection so that exp(H(P_i)) = perplexity (natural log),
+ *     stopping at |H - log perplexity| < 1e-5 or after 200 steps (the paper
+ *     gives no stopping rule);
+ *   p_ij = (p_{j|i} + p_{i|j}) / (2N), CSR with sorted columns, no diagonal.
+ * Distances are FP32 in difference form; neighbours are ordered by
+ * (distance, index); the bisection runs in FP64; values are rounded once to
+ * FP32. Every step is deterministic.
+ *
+ * tsne_affinity_create: workspace for N points of dimension D (1..64) and k
+ * neighbours (1..256, k < N, 2 N k < 2^31); all device memory (about
+ * 40 N k bytes) is allocated here; work is enqueued on stream (cudaStream_t,
+ * NULL = legacy default). INVALID_ARG on bad sizes, OOM.
+ * tsne_affinity_compute: X is DEVICE memory, N x D row-major FP32, read
+ * only; 1 <= perplexity <= k. Writes into *P_out a CSR that points into the
+ * workspace: valid until the next compute or destroy, owned by the
+ * workspace. Synchronises the stream (the host needs nnz).
+ * tsne_affinity_knn_copy: copies the last compute's neighbour lists
+ * (N x k, sorted by (d^2, index)), their squared distances and p_{j|i} to
+ * host buffers (any may be NULL). INVALID_ARG before the first compute.
+ */
+typedef struct tsne_affinity tsne_affinity;
+int tsne_affinity_create(int64_t N, int32_t D, int32_t k, void* stream, tsne_affinity** out);
+int tsne_affinity_destroy(tsne_affinity* aff);
+int tsne_affinity_compute(tsne_affinity* aff, const float* X, double perplexity, tsne_csr* P_out);
+int tsne_affinity_knn_copy(const tsne_affinity* aff, int32_t* idx_host, float* d2_host,
+                           double* pcond_host);
+/* Kernels the workspace has launched (host-side count). */
+int64_t tsne_affinity_launch_count(const tsne_affinity* aff);
+
+/*
  * KL(P || Q) without any device allocation (the paper has no counterpart;
  * this exists for callers that cannot call cudaMalloc, e.g. a process whose
  * own allocator owns all device memory, or code that must not let

@@ -27,7 +27,9 @@ __all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destr
            "tsne_batch_bytes_in_use", "tsne_batch_add_job", "tsne_batch_remove_job",
            "tsne_batch_iterate", "tsne_batch_poll", "tsne_batch_get_y", "tsne_batch_kl",
            "tsne_batch_set_tuning", "tsne_batch_get_tuning", "tsne_batch_autotune",
-           "tsne_batch_launch_count", "tsne_batch_stream"]
+           "tsne_batch_launch_count", "tsne_batch_stream", "Affinity", "tsne_affinity_create",
+           "tsne_affinity_destroy", "tsne_affinity_compute", "tsne_affinity_knn_copy",
+           "tsne_affinity_launch_count"]
 
 
 def lib():
@@ -218,6 +220,105 @@ def tsne_kl_noalloc(P: DeviceCSR, Y: torch.Tensor, s: int, Z: float, kl_out: tor
                                ctypes.c_void_p(stream))
     if rc != 0:
         raise TsneError(rc, lib().tsne_noalloc_last_error_string().decode())
+
+
+# ---- input affinities ------------------------------------------------------------
+
+def tsne_affinity_create(N: int, D: int, k: int, stream: int | None = None) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_void_p()
+    check(lib().tsne_affinity_create(N, D, k, ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out
+
+
+def tsne_affinity_destroy(aff) -> None:
+    check(lib().tsne_affinity_destroy(aff))
+
+
+def tsne_affinity_compute(aff, X: torch.Tensor, perplexity: float) -> _abi.tsne_csr:
+    if not (X.is_cuda and X.dtype == torch.float32 and X.is_contiguous() and X.dim() == 2):
+        raise TypeError("X must be a contiguous 2-D CUDA float32 tensor")
+    out = _abi.tsne_csr()
+    check(lib().tsne_affinity_compute(aff, _ptr(X), float(perplexity), ctypes.byref(out)))
+    return out
+
+
+def tsne_affinity_knn_copy(aff, idx=None, d2=None, pcond=None) -> None:
+    def host(a):
+        return None if a is None else ctypes.c_void_p(a.ctypes.data)
+    check(lib().tsne_affinity_knn_copy(aff, host(idx), host(d2), host(pcond)))
+
+
+def tsne_affinity_launch_count(aff) -> int:
+    return lib().tsne_affinity_launch_count(aff)
+
+
+class Affinity:
+    """Workspace for P from data X (N x D float32 on the device): exact kNN,
+    perplexity calibration and symmetrisation in the library's kernels.
+
+    compute() returns a DeviceCSR whose tensors view the workspace's memory:
+    valid until the next compute() or close()."""
+
+    def __init__(self, N: int, D: int, k: int, stream: int | None = None):
+        self.N, self.D, self.k = N, D, k
+        self._h = tsne_affinity_create(N, D, k, stream)
+
+    def compute(self, X: torch.Tensor, perplexity: float = 30.0) -> DeviceCSR:
+        if X.shape != (self.N, self.D):
+            raise ValueError(f"X must be {self.N} x {self.D}")
+        c = tsne_affinity_compute(self._h, X, perplexity)
+        dev = X.device
+
+        def view(ptr, n, dtype):
+            # a zero-copy view of workspace memory (kept alive by this object)
+            return _device_view(ptr, n, dtype, dev)
+        return DeviceCSR(view(c.row_ptr, self.N + 1, torch.int32), view(c.col, c.nnz, torch.int32),
+                         view(c.val, c.nnz, torch.float32))
+
+    def knn(self):
+        """(idx int32 N x k, d2 float32 N x k, p_{j|i} float64 N x k) of the last compute, on the host."""
+        idx = np.empty((self.N, self.k), np.int32)
+        d2 = np.empty((self.N, self.k), np.float32)
+        pc = np.empty((self.N, self.k), np.float64)
+        tsne_affinity_knn_copy(self._h, idx, d2, pc)
+        return idx, d2, pc
+
+    def launch_count(self) -> int:
+        return tsne_affinity_launch_count(self._h)
+
+    def close(self):
+        if self._h is not None:
+            tsne_affinity_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _device_view(ptr: int, n: int, dtype: torch.dtype, device) -> torch.Tensor:
+    """A torch tensor over n elements of library-owned device memory (no copy)."""
+    elem = torch.tensor([], dtype=dtype).element_size()
+
+    class _Iface:
+        __cuda_array_interface__ = {
+            "shape": (n,), "typestr": {torch.int32: "<i4", torch.float32: "<f4"}[dtype],
+            "data": (int(ptr or 0), False), "version": 3, "strides": None}
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device=device)
+    t = torch.as_tensor(_Iface(), device=device)
+    assert t.element_size() == elem
+    return t
 
 
 # ---- batched jobs ---------------------------------------------------------------

@@ -134,6 +134,12 @@ _SIGNATURES = [
     ("tsne_kl_noalloc", ctypes.c_int, [tsne_csr, _P, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_double, _P, _P]),
     ("tsne_noalloc_last_error_string", ctypes.c_char_p, []),
+    ("tsne_affinity_create", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+    ("tsne_affinity_destroy", ctypes.c_int, [_P]),
+    ("tsne_affinity_compute", ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(tsne_csr)]),
+    ("tsne_affinity_knn_copy", ctypes.c_int, [_P, _P, _P, _P]),
+    ("tsne_affinity_launch_count", ctypes.c_int64, [_P]),
 ]
 
 _lock = threading.Lock()

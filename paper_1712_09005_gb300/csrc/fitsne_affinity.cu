@@ -1,0 +1,716 @@
+// Input affinities P on the GPU (Sec. 1.1, Eq. p_ij, restricted to the k
+// exact nearest neighbours as in Sec. 3):
+//   p_{j|i} = exp(-beta_i |x_i - x_j|^2) / sum_{l in kNN(i)} exp(-beta_i |x_i - x_l|^2),
+//   beta_i by bisection so that exp(H(P_i)) = perplexity (natural log),
+//   p_ij = (p_{j|i} + p_{i|j}) / (2N), symmetric CSR with sorted columns.
+//
+//   knn_kernel        exact kNN, FP32 squared distances in difference form
+//                     (no cancellation); candidates streamed through shared
+//                     memory; each warp keeps the sorted top-k of 4 queries
+//                     (ties by the smaller index, as the oracle breaks them)
+//   calibrate_kernel  warp per row, FP64 bisection on beta (the oracle's rule:
+//                     start 1, double / halve while a side is open, else the
+//                     midpoint; stop at |H - log perplexity| < 1e-5 or 200 steps)
+//   radix kernels     stable LSD sort of the kNN edges (i -> j) by j: the
+//                     edges into each j, in increasing i
+//   symmetrise        per row the union of its out-list (sorted by column)
+//                     and in-list (sorted by source) by co-ranking, values
+//                     (p_{j|i} + p_{i|j}) / 2N in FP64 rounded once to FP32
+// Every step is deterministic.
+#include <limits.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "fitsne_internal.cuh"
+
+namespace fitsne {
+
+namespace {
+
+constexpr unsigned kFullA = 0xffffffffu;
+constexpr int kKnnTile = 128;     // candidates per shared-memory tile
+constexpr int kKnnQ = 8;          // queries per warp
+constexpr int kKnnWarps = 8;      // warps per CTA
+constexpr int kKnnDMax = 64;      // largest input dimension
+constexpr int kKnnKMax = 256;     // largest k
+constexpr int kRadixTile = 4096;  // items per radix-sort block
+constexpr int kRadixThreads = 256;
+
+// Shared-memory row stride in floats: a multiple of 4 (float4 reads) with an
+// odd number of float4s, so 8 lanes reading 8 consecutive rows hit 8
+// disjoint groups of 4 banks.
+__host__ __device__ __forceinline__ int knn_stride(int D) {
+    int Ds = (D + 3) / 4 * 4;
+    if ((Ds / 4) % 2 == 0) Ds += 4;
+    return Ds;
+}
+
+__host__ __forceinline__ size_t knn_smem_bytes(int D, int k) {
+    const size_t Ds = (size_t)knn_stride(D);
+    return sizeof(float) * (kKnnTile * Ds + (size_t)kKnnWarps * kKnnQ * Ds) +
+           (sizeof(float) + sizeof(int)) * (size_t)kKnnWarps * kKnnQ * k;
+}
+
+// (d, idx) lexicographic order: the kNN order of the oracle (stable sort of
+// distances by index).
+__device__ __forceinline__ bool knn_less(float d, int i, float e, int j) {
+    return d < e || (d == e && i < j);
+}
+
+// Inserts (d, i) into the sorted list (ld, li) of k entries held in shared
+// memory by the warp (lane-strided), dropping the last entry.
+__device__ __forceinline__ void knn_insert(float* ld, int* li, int k, float d, int i, int lane) {
+    // position = entries strictly before (d, i)
+    int pos = 0;
+    for (int m = lane; m < k; m += 32) pos += knn_less(ld[m], li[m], d, i) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) pos += __shfl_xor_sync(kFullA, pos, o);
+    // shift [pos, k - 1) right by one (read all, then write)
+    float vd[kKnnKMax / 32];
+    int vi[kKnnKMax / 32];
+#pragma unroll
+    for (int t = 0; t < kKnnKMax / 32; ++t) {
+        const int m = lane + 32 * t;
+        vd[t] = (m < k) ? ld[m] : 0.0f;
+        vi[t] = (m < k) ? li[m] : 0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kKnnKMax / 32; ++t) {
+        const int m = lane + 32 * t;
+        if (m >= pos && m + 1 < k) {
+            ld[m + 1] = vd[t];
+            li[m + 1] = vi[t];
+        }
+    }
+    if (lane == 0 && pos < k) {
+        ld[pos] = d;
+        li[pos] = i;
+    }
+    __syncwarp();
+}
+
+}  // namespace
+
+// Exact k nearest neighbours of queries [q0, q0 + nq) among all N points
+// (self excluded). X is N x D row-major. Output sorted by (d^2, index).
+__global__ void __launch_bounds__(kKnnWarps * 32)
+knn_kernel(const float* __restrict__ X, int64_t N, int D, int k, int64_t q0, int64_t nq,
+           int32_t* __restrict__ out_idx, float* __restrict__ out_d2) {
+    extern __shared__ float sm[];
+    const int Ds = knn_stride(D);
+    float* s_c = sm;                                     // [kKnnTile][Ds]
+    float* s_q = s_c + kKnnTile * Ds;                    // [kKnnWarps * kKnnQ][Ds]
+    float* s_ld = s_q + kKnnWarps * kKnnQ * Ds;          // [kKnnWarps * kKnnQ][k]
+    int* s_li = reinterpret_cast<int*>(s_ld + kKnnWarps * kKnnQ * k);
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    const int64_t nqb = (nq + kKnnWarps * kKnnQ - 1) / (kKnnWarps * kKnnQ);
+    for (int64_t qb = blockIdx.x; qb < nqb; qb += gridDim.x) {
+        const int64_t qbase = q0 + qb * kKnnWarps * kKnnQ;
+        __syncthreads();
+        for (int t = threadIdx.x; t < kKnnWarps * kKnnQ * Ds; t += blockDim.x) {
+            const int q = t / Ds, d = t - q * Ds;
+            const int64_t gq = qbase + q;
+            s_q[t] = (d < D && gq < q0 + nq) ? X[gq * D + d] : 0.0f;
+        }
+        for (int t = threadIdx.x; t < kKnnWarps * kKnnQ * k; t += blockDim.x) {
+            s_ld[t] = INFINITY;
+            s_li[t] = INT_MAX;
+        }
+        float thr[kKnnQ];
+        int thi[kKnnQ];
+#pragma unroll
+        for (int u = 0; u < kKnnQ; ++u) { thr[u] = INFINITY; thi[u] = INT_MAX; }
+        for (int64_t c0 = 0; c0 < N; c0 += kKnnTile) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < kKnnTile * Ds; t += blockDim.x) {
+                const int c = t / Ds, d = t - c * Ds;
+                const int64_t gc = c0 + c;
+                s_c[t] = (d < D && gc < N) ? X[gc * D + d] : 0.0f;
+            }
+            __syncthreads();
+            for (int cc = lane; cc < kKnnTile; cc += 32) {
+                const int64_t gc = c0 + cc;
+                float acc[kKnnQ];
+#pragma unroll
+                for (int u = 0; u < kKnnQ; ++u) acc[u] = 0.0f;
+                const float4* cv = reinterpret_cast<const float4*>(s_c + cc * Ds);
+                for (int d4 = 0; d4 < Ds / 4; ++d4) {
+                    const float4 c = cv[d4];
+#pragma unroll
+                    for (int u = 0; u < kKnnQ; ++u) {
+                        const float4 q = reinterpret_cast<const float4*>(s_q + (wid * kKnnQ + u) * Ds)[d4];
+                        const float a = q.x - c.x, b = q.y - c.y, e = q.z - c.z, f = q.w - c.w;
+                        acc[u] = fmaf(a, a, acc[u]);
+                        acc[u] = fmaf(b, b, acc[u]);
+                        acc[u] = fmaf(e, e, acc[u]);
+                        acc[u] = fmaf(f, f, acc[u]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kKnnQ; ++u) {
+                    // a non-finite distance ranks as +inf (by index among
+                    // equals), so every list fills with valid indices
+                    if (!(acc[u] <= 3.402823466e38f)) acc[u] = INFINITY;
+                    const int64_t gq = qbase + wid * kKnnQ + u;
+                    const bool ok = gc < N && gq < q0 + nq && gc != gq;
+                    const int ci = (int)gc;
+                    const bool take = ok && knn_less(acc[u], ci, thr[u], thi[u]);
+                    unsigned m = __ballot_sync(kFullA, take);
+                    float* ld = s_ld + (wid * kKnnQ + u) * k;
+                    int* li = s_li + (wid * kKnnQ + u) * k;
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        const float d = __shfl_sync(kFullA, acc[u], src);
+                        const int i = __shfl_sync(kFullA, ci, src);
+                        if (knn_less(d, i, thr[u], thi[u])) {
+                            knn_insert(ld, li, k, d, i, lane);
+                            thr[u] = ld[k - 1];
+                            thi[u] = li[k - 1];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < kKnnWarps * kKnnQ * k; t += blockDim.x) {
+            const int q = t / k, m = t - q * k;
+            const int64_t gq = qbase + q;
+            if (gq < q0 + nq) {
+                out_idx[gq * k + m] = s_li[t];
+                out_d2[gq * k + m] = s_ld[t];
+            }
+        }
+    }
+}
+
+// Bisection on beta per row (warp per row), FP64, the oracle's rule; writes
+// p_{j|i} (FP64) over the row's k neighbours.
+__global__ void calibrate_kernel(const float* __restrict__ d2, int64_t N, int k, double target,
+                                 double* __restrict__ pc) {
+    const int lane = threadIdx.x % 32;
+    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
+    constexpr int V = kKnnKMax / 32;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; i < N; i += nwarp) {
+        const float* row = d2 + i * k;
+        const double dmin = (double)row[0];  // the list is sorted: row[0] is the smallest
+        double x[V];
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+            const int m = lane + 32 * t;
+            x[t] = m < k ? (double)row[m] - dmin : 0.0;
+        }
+        double beta = 1.0, lo = -INFINITY, hi = INFINITY;
+        for (int it = 0; it < 200; ++it) {
+            double S = 0.0, W = 0.0;
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                if (lane + 32 * t < k) {
+                    const double e = exp(-beta * x[t]);
+                    S += e;
+                    W += e > 0.0 ? e * x[t] : 0.0;  // x = inf: no 0 * inf
+                }
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                S += __shfl_xor_sync(kFullA, S, o);
+                W += __shfl_xor_sync(kFullA, W, o);
+            }
+            const double H = log(S) + beta * (W / S);
+            if (fabs(H - target) < 1e-5) break;
+            if (H > target) {  // too flat: sharpen
+                lo = beta;
+                beta = isinf(hi) ? beta * 2.0 : (beta + hi) * 0.5;
+            } else {
+                hi = beta;
+                beta = isinf(lo) ? beta * 0.5 : (beta + lo) * 0.5;
+            }
+        }
+        double S = 0.0;
+        double e[V];
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+            e[t] = (lane + 32 * t < k) ? exp(-beta * x[t]) : 0.0;
+            S += e[t];
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) S += __shfl_xor_sync(kFullA, S, o);
+#pragma unroll
+        for (int t = 0; t < V; ++t)
+            if (lane + 32 * t < k) pc[i * k + lane + 32 * t] = e[t] / S;
+    }
+}
+
+// ---- stable LSD radix sort of (key, item) pairs by key, 8 bits per pass ----
+
+// Per tile digit counts, digit-major: counts[digit * nblocks + block].
+__global__ void __launch_bounds__(kRadixThreads)
+radix_count_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                   uint32_t* __restrict__ counts, int nblocks) {
+    __shared__ uint32_t h[256];
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        __syncthreads();
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t e0 = (int64_t)b * kRadixTile;
+        for (int t = threadIdx.x; t < kRadixTile; t += blockDim.x) {
+            const int64_t e = e0 + t;
+            if (e < n) atomicAdd(&h[(keys[e] >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        counts[(int64_t)threadIdx.x * nblocks + b] = h[threadIdx.x];
+    }
+}
+
+// Exclusive scan of n values in place (one CTA of 1024 threads, chunked).
+__global__ void __launch_bounds__(1024) scan_inplace_kernel(uint32_t* __restrict__ a, int64_t n) {
+    __shared__ uint32_t sw[32];
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    for (int64_t base = 0; base < n; base += 4 * 1024) {
+        uint32_t v[4], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t e = base + threadIdx.x * 4 + q;
+            v[q] = e < n ? a[e] : 0u;
+            sum += v[q];
+        }
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullA, x, o);
+            if (lane >= o) x += y;
+        }
+        __syncthreads();
+        if (lane == 31) sw[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t t = sw[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFullA, t, o);
+                if (lane >= o) t += y;
+            }
+            sw[lane] = t;
+        }
+        __syncthreads();
+        uint32_t run = s_carry + x - sum + (wid ? sw[wid - 1] : 0u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t e = base + threadIdx.x * 4 + q;
+            if (e < n) a[e] = run;
+            run += v[q];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += sw[31];
+    }
+}
+
+// Places each item at its digit's offset for the block plus its stable rank
+// within the block (items are visited in order, 256 at a time; in a warp the
+// rank among equal digits comes from match_any; across the warps of a chunk,
+// per-digit counts are scanned in warp order).
+__global__ void __launch_bounds__(kRadixThreads)
+radix_scatter_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ items,
+                     int64_t n, int shift, const uint32_t* __restrict__ offsets, int nblocks,
+                     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ items_out) {
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wcnt[kRadixThreads / 32][256];
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        __syncthreads();
+        run[threadIdx.x] = offsets[(int64_t)threadIdx.x * nblocks + b];
+        const int64_t e0 = (int64_t)b * kRadixTile;
+        for (int c = 0; c < kRadixTile; c += kRadixThreads) {
+            for (int t = threadIdx.x; t < (kRadixThreads / 32) * 256; t += blockDim.x)
+                (&wcnt[0][0])[t] = 0;
+            __syncthreads();
+            const int64_t e = e0 + c + threadIdx.x;
+            const bool in = e < n;
+            const uint32_t key = in ? keys[e] : 0u;
+            const uint32_t item = in ? items[e] : 0u;
+            const int dg = in ? (int)((key >> shift) & 255u) : 256;
+            const unsigned peers = __match_any_sync(kFullA, dg);
+            const int rank_w = __popc(peers & lt);
+            if (in && rank_w == 0) wcnt[wid][dg] = __popc(peers);
+            __syncthreads();
+            if (in) {
+                uint32_t before = 0;
+                for (int w = 0; w < wid; ++w) before += wcnt[w][dg];
+                const uint32_t pos = run[dg] + before + rank_w;
+                keys_out[pos] = key;
+                items_out[pos] = item;
+            }
+            __syncthreads();
+            // advance the running offsets by this chunk's counts
+            {
+                const int d = threadIdx.x;
+                uint32_t tot = 0;
+                for (int w = 0; w < kRadixThreads / 32; ++w) tot += wcnt[w][d];
+                run[d] += tot;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---- symmetrisation ----
+
+__global__ void edge_keys_kernel(const int32_t* __restrict__ knn_idx, int64_t nk,
+                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ items) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        keys[e] = (uint32_t)knn_idx[e];  // target j
+        items[e] = (uint32_t)e;          // edge id = i * k + m
+    }
+}
+
+// in_ptr[j] = first sorted edge whose target is j (keys sorted): binary search
+__global__ void in_ptr_kernel(const uint32_t* __restrict__ sorted_keys, int64_t nk, int64_t N,
+                              int32_t* __restrict__ in_ptr) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= N;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nk;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if ((int64_t)sorted_keys[mid] < j) lo = mid + 1;
+            else hi = mid;
+        }
+        in_ptr[j] = (int32_t)lo;
+    }
+}
+
+// Per row i (warp): its out-list O sorted by column (bitonic in shared
+// memory, k <= 256) and its in-list I (edges into i, sources increasing,
+// from the stable sort). flag[m] = O[m] is also in I; F[m] = flags before m.
+// Pass 0 writes the union's size k + |I| - F[k]; pass 1 writes the union in
+// column order by co-ranking:
+//   out-entry O[m] = j      -> m + #{s in I : s < j} - F[m]
+//   in-only entry I[t] = s  -> #{o in O : o < s} + t - F[#{o in O : o < s}]
+__global__ void __launch_bounds__(256)
+symmetrise_kernel(const int32_t* __restrict__ knn_idx, const double* __restrict__ pc, int64_t N,
+                  int k, const int32_t* __restrict__ in_ptr, const uint32_t* __restrict__ in_edge,
+                  int pass, int32_t* __restrict__ row_len, const int32_t* __restrict__ row_ptr,
+                  int32_t* __restrict__ col, float* __restrict__ val) {
+    __shared__ int s_col[8][kKnnKMax];
+    __shared__ double s_val[8][kKnnKMax];
+    __shared__ int s_in[8][kKnnKMax];   // per out-entry: position in I, or -1
+    __shared__ int s_F[8][kKnnKMax + 1];
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
+    const double inv2n = 1.0 / (2.0 * (double)N);
+    int* oc = s_col[wid];
+    double* ov = s_val[wid];
+    int* oin = s_in[wid];
+    int* F = s_F[wid];
+    const uint32_t uk = (uint32_t)k;
+    int M = 1;
+    while (M < k) M <<= 1;
+    const int V = (k + 31) / 32;  // contiguous out-entries per lane for the prefix
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; i < N; i += nwarp) {
+        for (int m = lane; m < M; m += 32) {
+            oc[m] = m < k ? knn_idx[i * k + m] : INT_MAX;
+            ov[m] = m < k ? pc[i * k + m] : 0.0;
+        }
+        __syncwarp();
+        for (int kk = 2; kk <= M; kk <<= 1)
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (int a = lane; a < M; a += 32) {
+                    const int b = a ^ jj;
+                    if (b > a) {
+                        const bool up = (a & kk) == 0;
+                        if ((oc[a] > oc[b]) == up) {
+                            const int tc = oc[a]; oc[a] = oc[b]; oc[b] = tc;
+                            const double tv = ov[a]; ov[a] = ov[b]; ov[b] = tv;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        const int i0 = in_ptr[i], nin = in_ptr[i + 1] - i0;
+        const uint32_t* ie = in_edge + i0;
+        // flags and in-positions of the out-entries
+        for (int m = lane; m < k; m += 32) {
+            const int j = oc[m];
+            int lo = 0, hi = nin;
+            while (lo < hi) {
+                const int mid = (lo + hi) / 2;
+                if ((int)(ie[mid] / uk) < j) lo = mid + 1;
+                else hi = mid;
+            }
+            oin[m] = (lo < nin && (int)(ie[lo] / uk) == j) ? lo : -1;
+        }
+        __syncwarp();
+        // F = exclusive prefix of the flags (lane owns [lane V, lane V + V))
+        int cnt = 0;
+        for (int q = 0; q < V; ++q) {
+            const int m = lane * V + q;
+            cnt += (m < k && oin[m] >= 0) ? 1 : 0;
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFullA, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int run = incl - cnt;
+        for (int q = 0; q < V; ++q) {
+            const int m = lane * V + q;
+            if (m < k) {
+                F[m] = run;
+                run += oin[m] >= 0 ? 1 : 0;
+            }
+        }
+        if (lane == 31) F[k] = incl;
+        __syncwarp();
+        const int matched = F[k];
+        if (pass == 0) {
+            if (lane == 0) row_len[i] = k + nin - matched;
+        } else {
+            const int64_t base = row_ptr[i];
+            for (int m = lane; m < k; m += 32) {
+                const int j = oc[m];
+                double v = ov[m];
+                int less_in;
+                if (oin[m] >= 0) {
+                    less_in = oin[m];
+                    v += pc[ie[less_in]];
+                } else {
+                    int lo = 0, hi = nin;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) / 2;
+                        if ((int)(ie[mid] / uk) < j) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    less_in = lo;
+                }
+                const int64_t pos = base + m + less_in - F[m];
+                col[pos] = j;
+                val[pos] = (float)(v * inv2n);
+            }
+            for (int t = lane; t < nin; t += 32) {
+                const uint32_t ed = ie[t];
+                const int s = (int)(ed / uk);
+                int lo = 0, hi = k;
+                while (lo < hi) {
+                    const int mid = (lo + hi) / 2;
+                    if (oc[mid] < s) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (lo < k && oc[lo] == s) continue;  // written with its out-entry
+                const int64_t pos = base + lo + t - F[lo];
+                col[pos] = s;
+                val[pos] = (float)(pc[ed] * inv2n);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace fitsne
+
+// ----------------------------------------------------------------------------
+// C ABI
+// ----------------------------------------------------------------------------
+struct tsne_affinity {
+    int64_t N = 0;
+    int D = 0, k = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    int32_t* knn_idx = nullptr;   // [N k]
+    float* knn_d2 = nullptr;      // [N k]
+    double* pc = nullptr;         // [N k] p_{j|i}
+    uint32_t* keys[2] = {nullptr, nullptr};
+    uint32_t* items[2] = {nullptr, nullptr};
+    uint32_t* counts = nullptr;   // [256 nblocks]
+    int32_t* in_ptr = nullptr;    // [N + 1]
+    int32_t* row_ptr = nullptr;   // [N + 1]
+    int32_t* col = nullptr;       // [2 N k]
+    float* val = nullptr;         // [2 N k]
+    int64_t nnz = -1;             // of the last compute
+    int64_t launches = 0;
+};
+
+namespace {
+
+int aff_cuda_fail(cudaError_t e, const char* what) {
+    return fitsne::set_error(TSNE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define ACU(call, what)                                          \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return aff_cuda_fail(e_, what);   \
+    } while (0)
+
+void free_affinity(tsne_affinity* a) {
+    if (!a) return;
+    void* ps[] = {a->knn_idx, a->knn_d2, a->pc, a->keys[0], a->keys[1], a->items[0], a->items[1],
+                  a->counts, a->in_ptr, a->row_ptr, a->col, a->val};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    delete a;
+}
+
+template <typename T>
+int aff_alloc(T** p, size_t count, const char* what) {
+    *p = nullptr;
+    if (cudaMalloc((void**)p, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fitsne::set_error(TSNE_ERR_OOM, "cudaMalloc of %zu bytes for %s failed",
+                                 count * sizeof(T), what);
+    }
+    return TSNE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsne_affinity_create(int64_t N, int32_t D, int32_t k, void* stream, tsne_affinity** out) {
+    fitsne::clear_error();
+    if (!out) return fitsne::set_error(TSNE_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (D < 1 || D > fitsne::kKnnDMax)
+        return fitsne::set_error(TSNE_ERR_INVALID_ARG, "D = %d outside [1, %d]", D, fitsne::kKnnDMax);
+    if (k < 1 || k > fitsne::kKnnKMax)
+        return fitsne::set_error(TSNE_ERR_INVALID_ARG, "k = %d outside [1, %d]", k, fitsne::kKnnKMax);
+    if (N < 2 || N <= k)
+        return fitsne::set_error(TSNE_ERR_INVALID_ARG, "N = %lld must exceed k = %d", (long long)N, k);
+    const int64_t nk = N * (int64_t)k;
+    if (2 * nk > INT32_MAX)  // edge ids (i k + m) and CSR offsets are 32-bit
+        return fitsne::set_error(TSNE_ERR_INVALID_ARG, "2 N k = %lld exceeds 2^31 - 1", (long long)(2 * nk));
+    tsne_affinity* a = new tsne_affinity();
+    a->N = N;
+    a->D = D;
+    a->k = k;
+    a->stream = (cudaStream_t)stream;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&a->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) { free_affinity(a); return aff_cuda_fail(ce, "device setup"); }
+    const int64_t nblocks = (nk + fitsne::kRadixTile - 1) / fitsne::kRadixTile;
+    int rc = TSNE_OK;
+    if (!rc) rc = aff_alloc(&a->knn_idx, (size_t)nk, "kNN indices");
+    if (!rc) rc = aff_alloc(&a->knn_d2, (size_t)nk, "kNN distances");
+    if (!rc) rc = aff_alloc(&a->pc, (size_t)nk, "conditional affinities");
+    for (int b = 0; b < 2 && !rc; ++b) {
+        rc = aff_alloc(&a->keys[b], (size_t)nk, "sort keys");
+        if (!rc) rc = aff_alloc(&a->items[b], (size_t)nk, "sort items");
+    }
+    if (!rc) rc = aff_alloc(&a->counts, (size_t)(256 * nblocks), "digit counts");
+    if (!rc) rc = aff_alloc(&a->in_ptr, (size_t)(N + 1), "in-list offsets");
+    if (!rc) rc = aff_alloc(&a->row_ptr, (size_t)(N + 1), "row_ptr");
+    if (!rc) rc = aff_alloc(&a->col, (size_t)(2 * nk), "col");
+    if (!rc) rc = aff_alloc(&a->val, (size_t)(2 * nk), "val");
+    if (rc) { free_affinity(a); return rc; }
+    *out = a;
+    return TSNE_OK;
+}
+
+int tsne_affinity_destroy(tsne_affinity* a) {
+    fitsne::clear_error();
+    if (!a) return TSNE_OK;
+    cudaStreamSynchronize(a->stream);
+    free_affinity(a);
+    return TSNE_OK;
+}
+
+int tsne_affinity_compute(tsne_affinity* a, const float* X, double perplexity, tsne_csr* P_out) {
+    fitsne::clear_error();
+    if (!a) return fitsne::set_error(TSNE_ERR_INVALID_ARG, "affinity object is NULL");
+    if (!X || !P_out) return fitsne::set_error(TSNE_ERR_INVALID_ARG, "X or P_out is NULL");
+    if (!(perplexity >= 1.0) || !(perplexity <= (double)a->k))
+        return fitsne::set_error(TSNE_ERR_INVALID_ARG, "perplexity %g outside [1, k = %d]", perplexity, a->k);
+    using namespace fitsne;
+    const int64_t N = a->N, nk = N * (int64_t)a->k;
+    const int k = a->k;
+    cudaStream_t st = a->stream;
+    a->nnz = -1;
+    // 1. exact kNN
+    {
+        const int64_t nqb = (N + kKnnWarps * kKnnQ - 1) / (kKnnWarps * kKnnQ);
+        const int grid = (int)std::min<int64_t>(nqb, 64LL * a->sm_count);
+        // a per-function attribute: set for this workspace's size at each launch
+        ACU(cudaFuncSetAttribute(knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)knn_smem_bytes(a->D, k)),
+            "kNN shared memory");
+        knn_kernel<<<grid, kKnnWarps * 32, knn_smem_bytes(a->D, k), st>>>(X, N, a->D, k, 0, N, a->knn_idx,
+                                                                           a->knn_d2);
+        ACU(cudaGetLastError(), "kNN launch");
+    }
+    // 2. bandwidths
+    {
+        const int grid = (int)std::min<int64_t>((N + 7) / 8, 16LL * a->sm_count);
+        calibrate_kernel<<<grid, 256, 0, st>>>(a->knn_d2, N, k, log(perplexity), a->pc);
+        ACU(cudaGetLastError(), "calibrate launch");
+    }
+    // 3. edges sorted by target (stable: sources increasing within a target)
+    const int nblocks = (int)((nk + kRadixTile - 1) / kRadixTile);
+    const int rgrid = std::min(nblocks, 8 * a->sm_count);
+    {
+        const int grid = (int)std::min<int64_t>((nk + 255) / 256, 8LL * a->sm_count);
+        edge_keys_kernel<<<grid, 256, 0, st>>>(a->knn_idx, nk, a->keys[0], a->items[0]);
+        ACU(cudaGetLastError(), "edge keys launch");
+    }
+    int bits = 1;
+    while (bits < 31 && ((N - 1) >> bits) != 0) ++bits;
+    int cur = 0, passes = 0;
+    for (int shift = 0; shift < bits; shift += 8, ++passes) {
+        radix_count_kernel<<<rgrid, kRadixThreads, 0, st>>>(a->keys[cur], nk, shift, a->counts, nblocks);
+        scan_inplace_kernel<<<1, 1024, 0, st>>>(a->counts, 256LL * nblocks);
+        radix_scatter_kernel<<<rgrid, kRadixThreads, 0, st>>>(a->keys[cur], a->items[cur], nk, shift, a->counts,
+                                                               nblocks, a->keys[cur ^ 1], a->items[cur ^ 1]);
+        ACU(cudaGetLastError(), "radix pass launch");
+        cur ^= 1;
+    }
+    {
+        const int grid = (int)std::min<int64_t>((N + 256) / 256, 8LL * a->sm_count);
+        in_ptr_kernel<<<grid, 256, 0, st>>>(a->keys[cur], nk, N, a->in_ptr);
+        ACU(cudaGetLastError(), "in-list offsets launch");
+    }
+    // 4. symmetrise: union sizes, offsets, union
+    const int sgrid = (int)std::min<int64_t>((N + 7) / 8, 16LL * a->sm_count);
+    symmetrise_kernel<<<sgrid, 256, 0, st>>>(a->knn_idx, a->pc, N, k, a->in_ptr, a->items[cur], 0, a->row_ptr,
+                                             nullptr, nullptr, nullptr);
+    ACU(cudaMemsetAsync(a->row_ptr + N, 0, sizeof(int32_t), st), "row_ptr tail");
+    scan_inplace_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<uint32_t*>(a->row_ptr), N + 1);
+    symmetrise_kernel<<<sgrid, 256, 0, st>>>(a->knn_idx, a->pc, N, k, a->in_ptr, a->items[cur], 1, nullptr,
+                                             a->row_ptr, a->col, a->val);
+    ACU(cudaGetLastError(), "symmetrise launch");
+    a->launches += 7 + 3 * passes;
+    int32_t nnz = 0;
+    ACU(cudaMemcpyAsync(&nnz, a->row_ptr + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "nnz read-back");
+    ACU(cudaStreamSynchronize(st), "affinity synchronise");
+    a->nnz = nnz;
+    P_out->row_ptr = a->row_ptr;
+    P_out->col = a->col;
+    P_out->val = a->val;
+    P_out->nnz = nnz;
+    return TSNE_OK;
+}
+
+int tsne_affinity_knn_copy(const tsne_affinity* a, int32_t* idx_host, float* d2_host, double* pcond_host) {
+    fitsne::clear_error();
+    if (!a) return fitsne::set_error(TSNE_ERR_INVALID_ARG, "affinity object is NULL");
+    if (a->nnz < 0) return fitsne::set_error(TSNE_ERR_INVALID_ARG, "no affinities computed yet");
+    const size_t nk = (size_t)a->N * (size_t)a->k;
+    if (idx_host)
+        ACU(cudaMemcpyAsync(idx_host, a->knn_idx, nk * sizeof(int32_t), cudaMemcpyDeviceToHost, a->stream), "copy");
+    if (d2_host)
+        ACU(cudaMemcpyAsync(d2_host, a->knn_d2, nk * sizeof(float), cudaMemcpyDeviceToHost, a->stream), "copy");
+    if (pcond_host)
+        ACU(cudaMemcpyAsync(pcond_host, a->pc, nk * sizeof(double), cudaMemcpyDeviceToHost, a->stream), "copy");
+    ACU(cudaStreamSynchronize(a->stream), "copy synchronise");
+    return TSNE_OK;
+}
+
+int64_t tsne_affinity_launch_count(const tsne_affinity* a) { return a ? a->launches : 0; }
+
+}  // extern "C"

@@ -72,3 +72,30 @@ def test_null_plan_is_rejected(lib):
     assert lib.tsne_plan_destroy(None) == 0
     assert lib.tsne_plan_status(None) == _abi.TSNE_ERR_INVALID_ARG
     assert lib.tsne_plan_launch_count(None) == 0
+
+
+@pytest.mark.parametrize("N,D,k", [
+    (100, 0, 10),      # D < 1
+    (100, 65, 10),     # D > 64
+    (100, 50, 0),      # k < 1
+    (1000, 50, 257),   # k > 256
+    (90, 50, 90),      # N <= k
+    (1, 3, 1),         # N < 2
+    (20_000_000, 50, 90),  # 2 N k above 2^31 - 1
+])
+def test_affinity_create_rejects_bad_arguments(lib, N, D, k):
+    from paper_1712_09005_gb300 import _abi
+    out = ctypes.c_void_p(1)
+    rc = lib.tsne_affinity_create(N, D, k, None, ctypes.byref(out))
+    assert rc == _abi.TSNE_ERR_INVALID_ARG
+    assert out.value is None
+    assert lib.tsne_last_error_string()
+
+
+def test_null_affinity_is_rejected(lib):
+    from paper_1712_09005_gb300 import _abi
+    assert lib.tsne_affinity_destroy(None) == 0
+    csr = _abi.tsne_csr()
+    assert lib.tsne_affinity_compute(None, None, 30.0, ctypes.byref(csr)) == _abi.TSNE_ERR_INVALID_ARG
+    assert lib.tsne_affinity_knn_copy(None, None, None, None) == _abi.TSNE_ERR_INVALID_ARG
+    assert lib.tsne_affinity_launch_count(None) == 0
