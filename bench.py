@@ -9,7 +9,7 @@ region is the whole 1000-iteration job of the N = 1,000,000, s = 2 workload
 first on a scratch copy of the same job.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload n1m_2d|n1m_1d|n100k_2d|n2k_2d|served]
+                  [--workload n1m_2d|n1m_1d|n100k_2d|n2k_2d|served|affinity]
 
 The same JSON line also carries two sub-measurements of the batched forms:
   "batched": 64 independent jobs (N log-uniform in [1k, 200k], s = 2, 1000
@@ -22,6 +22,8 @@ The same JSON line also carries two sub-measurements of the batched forms:
              perplexity in {10, 30, 50}, 1000 iterations each, admitted
              under a 40 GB HBM budget; p50/p99 latency and embeddings/s.
              --workload served runs the whole 500-job stream instead.
+--workload affinity times the GPU construction of P itself (exact kNN,
+bandwidths, symmetrisation) for the N = 1M, D = 50 mixture.
 
 Under torchrun each rank runs its own independent job (its own seed): the
 method shards by job with no data-path exchange, so scaling is weak and
@@ -542,13 +544,88 @@ def run_served_only(a):
     return 0
 
 
+def run_affinity(a):
+    """--workload affinity: P from X on the GPU (exact kNN k = 90, perplexity
+    30, symmetrisation) for the N = 1M, D = 50 mixture of n1m_2d (rank 0 only).
+    The roofline line is the kNN kernel's: 3 flops (subtract, multiply, add)
+    per pair and dimension over N (N - 1) D against the FP32 lanes' rate for
+    that mix (152 SMs x 128 lanes x 1.5 flops per instruction x the sampled
+    SM clock)."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1712_09005_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1712_09005_gb300 as pkg
+    from paper_1712_09005_gb300 import inputs
+    N = a.n or 1_000_000
+    args = inputs.mixture_args(3, N=N)
+    X = inputs.mixture(**args)
+    D, k, perp = X.shape[1], 90, 30.0
+    Xd = torch.as_tensor(X, device="cuda")
+    warm, steps = max(3, a.warmup), a.steps
+    sampler = ClockSampler(local)
+    with pkg.Affinity(N, D, k) as aff:
+        for _ in range(warm):
+            aff.compute(Xd, perp)
+        phases = []
+        launches0 = aff.launch_count()
+        sampler.start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            P = aff.compute(Xd, perp)  # synchronises (nnz)
+            phases.append(aff.phase_ms())
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop()
+        launches = aff.launch_count() - launches0
+        nnz = P.nnz
+        # end to end: X from pinned host memory, P back to pinned host memory
+        Xh = torch.from_numpy(X).pin_memory()
+        rp_h = torch.empty(N + 1, dtype=torch.int32).pin_memory()
+        col_h = torch.empty(2 * N * k, dtype=torch.int32).pin_memory()
+        val_h = torch.empty(2 * N * k, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(steps):
+            Xd.copy_(Xh, non_blocking=True)
+            P = aff.compute(Xd, perp)
+            rp_h.copy_(P.row_ptr, non_blocking=True)
+            col_h[:P.nnz].copy_(P.col, non_blocking=True)
+            val_h[:P.nnz].copy_(P.val, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_wall = time.perf_counter() - t1
+    ms = {kk: statistics.median(ph[kk] for ph in phases) for kk in phases[0]}
+    total_ms = sum(ms.values())
+    clk = clocks.get("sm_mhz") or 2070.0
+    peak = 152 * 128 * 1.5 * clk * 1e6 / 1e12  # TFLOP/s for the sub + fma mix
+    achieved = 3.0 * N * (N - 1) * D / (ms["knn"] * 1e-3) / 1e12
+    line = {"metric": "affinity builds/s (exact kNN k=90, perplexity 30, N=1M, D=50)",
+            "value": 1e3 / total_ms, "unit": "builds/s", "n_gpus": 1, "steps": steps, "warmup": warm,
+            "ms_per_step": total_ms, "higher_is_better": True, "dtype": "f32 (kNN), f64 (bandwidths)",
+            "data": "synthetic", "config": {"workload": f"N={N} 50-d mixture (100 clusters + 5% background), "
+                                                      "k=90, perplexity 30", "l2": "inputs larger than L2"},
+            "phases_ms": ms, "nnz": nnz, "wall_s_per_step": wall / steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_basis": f"152 SMs x 128 FP32 lanes x 1.5 flop/instr x {clk:.0f} MHz (sampled)"},
+            "e2e": {"value": steps / e2e_wall, "unit": "builds/s", "h2d_bytes_per_step": X.nbytes,
+                    "d2h_bytes_per_step": 4 * (N + 1) + 8 * nnz},
+            "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps [1000 iterations; 3 builds for --workload affinity]")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served"], default="n1m_2d")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served", "affinity"], default="n1m_2d")
     ap.add_argument("--n", type=int, default=0, help="override the workload's N (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -563,10 +640,14 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle iterations the reference arm times")
     a = ap.parse_args()
+    if a.steps is None:
+        a.steps = 3 if a.workload == "affinity" else 1000
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "served":
         return run_served_only(a)
+    if a.workload == "affinity":
+        return run_affinity(a)
     return run_ours(a)
 
 

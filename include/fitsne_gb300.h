@@ -420,6 +420,10 @@ int tsne_affinity_destroy(tsne_affinity* aff);
 int tsne_affinity_compute(tsne_affinity* aff, const float* X, double perplexity, tsne_csr* P_out);
 int tsne_affinity_knn_copy(const tsne_affinity* aff, int32_t* idx_host, float* d2_host,
                            double* pcond_host);
+/* Device time (CUDA events on the workspace's stream) of the last compute's
+ * phases: ms_out[0] kNN, [1] bandwidths, [2] edge sort, [3] symmetrisation.
+ * INVALID_ARG before the first compute. */
+int tsne_affinity_phase_ms(const tsne_affinity* aff, double* ms_out);
 /* Kernels the workspace has launched (host-side count). */
 int64_t tsne_affinity_launch_count(const tsne_affinity* aff);
 

@@ -29,7 +29,7 @@ __all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destr
            "tsne_batch_set_tuning", "tsne_batch_get_tuning", "tsne_batch_autotune",
            "tsne_batch_launch_count", "tsne_batch_stream", "Affinity", "tsne_affinity_create",
            "tsne_affinity_destroy", "tsne_affinity_compute", "tsne_affinity_knn_copy",
-           "tsne_affinity_launch_count"]
+           "tsne_affinity_phase_ms", "tsne_affinity_launch_count"]
 
 
 def lib():
@@ -250,6 +250,12 @@ def tsne_affinity_knn_copy(aff, idx=None, d2=None, pcond=None) -> None:
     check(lib().tsne_affinity_knn_copy(aff, host(idx), host(d2), host(pcond)))
 
 
+def tsne_affinity_phase_ms(aff) -> list[float]:
+    ms = (ctypes.c_double * 4)()
+    check(lib().tsne_affinity_phase_ms(aff, ms))
+    return list(ms)
+
+
 def tsne_affinity_launch_count(aff) -> int:
     return lib().tsne_affinity_launch_count(aff)
 
@@ -287,6 +293,10 @@ class Affinity:
 
     def launch_count(self) -> int:
         return tsne_affinity_launch_count(self._h)
+
+    def phase_ms(self) -> dict:
+        """Device time of the last compute's phases (CUDA events on its stream)."""
+        return dict(zip(("knn", "bandwidths", "edge_sort", "symmetrise"), tsne_affinity_phase_ms(self._h)))
 
     def close(self):
         if self._h is not None:

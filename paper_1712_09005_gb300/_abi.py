@@ -139,6 +139,7 @@ _SIGNATURES = [
     ("tsne_affinity_destroy", ctypes.c_int, [_P]),
     ("tsne_affinity_compute", ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(tsne_csr)]),
     ("tsne_affinity_knn_copy", ctypes.c_int, [_P, _P, _P, _P]),
+    ("tsne_affinity_phase_ms", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("tsne_affinity_launch_count", ctypes.c_int64, [_P]),
 ]
 

@@ -534,6 +534,7 @@ struct tsne_affinity {
     float* val = nullptr;         // [2 N k]
     int64_t nnz = -1;             // of the last compute
     int64_t launches = 0;
+    cudaEvent_t ev[5] = {};       // phase boundaries of the last compute
 };
 
 namespace {
@@ -554,6 +555,8 @@ void free_affinity(tsne_affinity* a) {
                   a->counts, a->in_ptr, a->row_ptr, a->col, a->val};
     for (void* p : ps)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : a->ev)
+        if (e) cudaEventDestroy(e);
     delete a;
 }
 
@@ -594,6 +597,7 @@ int tsne_affinity_create(int64_t N, int32_t D, int32_t k, void* stream, tsne_aff
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&a->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    for (int e = 0; e < 5 && ce == cudaSuccess; ++e) ce = cudaEventCreate(&a->ev[e]);
     if (ce != cudaSuccess) { free_affinity(a); return aff_cuda_fail(ce, "device setup"); }
     const int64_t nblocks = (nk + fitsne::kRadixTile - 1) / fitsne::kRadixTile;
     int rc = TSNE_OK;
@@ -633,6 +637,7 @@ int tsne_affinity_compute(tsne_affinity* a, const float* X, double perplexity, t
     const int k = a->k;
     cudaStream_t st = a->stream;
     a->nnz = -1;
+    ACU(cudaEventRecord(a->ev[0], st), "event");
     // 1. exact kNN
     {
         const int64_t nqb = (N + kKnnWarps * kKnnQ - 1) / (kKnnWarps * kKnnQ);
@@ -645,12 +650,14 @@ int tsne_affinity_compute(tsne_affinity* a, const float* X, double perplexity, t
                                                                            a->knn_d2);
         ACU(cudaGetLastError(), "kNN launch");
     }
+    ACU(cudaEventRecord(a->ev[1], st), "event");
     // 2. bandwidths
     {
         const int grid = (int)std::min<int64_t>((N + 7) / 8, 16LL * a->sm_count);
         calibrate_kernel<<<grid, 256, 0, st>>>(a->knn_d2, N, k, log(perplexity), a->pc);
         ACU(cudaGetLastError(), "calibrate launch");
     }
+    ACU(cudaEventRecord(a->ev[2], st), "event");
     // 3. edges sorted by target (stable: sources increasing within a target)
     const int nblocks = (int)((nk + kRadixTile - 1) / kRadixTile);
     const int rgrid = std::min(nblocks, 8 * a->sm_count);
@@ -675,6 +682,7 @@ int tsne_affinity_compute(tsne_affinity* a, const float* X, double perplexity, t
         in_ptr_kernel<<<grid, 256, 0, st>>>(a->keys[cur], nk, N, a->in_ptr);
         ACU(cudaGetLastError(), "in-list offsets launch");
     }
+    ACU(cudaEventRecord(a->ev[3], st), "event");
     // 4. symmetrise: union sizes, offsets, union
     const int sgrid = (int)std::min<int64_t>((N + 7) / 8, 16LL * a->sm_count);
     symmetrise_kernel<<<sgrid, 256, 0, st>>>(a->knn_idx, a->pc, N, k, a->in_ptr, a->items[cur], 0, a->row_ptr,
@@ -684,6 +692,7 @@ int tsne_affinity_compute(tsne_affinity* a, const float* X, double perplexity, t
     symmetrise_kernel<<<sgrid, 256, 0, st>>>(a->knn_idx, a->pc, N, k, a->in_ptr, a->items[cur], 1, nullptr,
                                              a->row_ptr, a->col, a->val);
     ACU(cudaGetLastError(), "symmetrise launch");
+    ACU(cudaEventRecord(a->ev[4], st), "event");
     a->launches += 7 + 3 * passes;
     int32_t nnz = 0;
     ACU(cudaMemcpyAsync(&nnz, a->row_ptr + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "nnz read-back");
@@ -708,6 +717,18 @@ int tsne_affinity_knn_copy(const tsne_affinity* a, int32_t* idx_host, float* d2_
     if (pcond_host)
         ACU(cudaMemcpyAsync(pcond_host, a->pc, nk * sizeof(double), cudaMemcpyDeviceToHost, a->stream), "copy");
     ACU(cudaStreamSynchronize(a->stream), "copy synchronise");
+    return TSNE_OK;
+}
+
+int tsne_affinity_phase_ms(const tsne_affinity* a, double* ms_out) {
+    fitsne::clear_error();
+    if (!a || !ms_out) return fitsne::set_error(TSNE_ERR_INVALID_ARG, "affinity object or ms_out is NULL");
+    if (a->nnz < 0) return fitsne::set_error(TSNE_ERR_INVALID_ARG, "no affinities computed yet");
+    for (int e = 0; e < 4; ++e) {
+        float ms = 0.0f;
+        ACU(cudaEventElapsedTime(&ms, a->ev[e], a->ev[e + 1]), "event time");
+        ms_out[e] = ms;
+    }
     return TSNE_OK;
 }
 
