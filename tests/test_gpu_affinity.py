@@ -141,6 +141,10 @@ def test_k_is_everyone_else_and_k_at_maximum():
     # k = 256 (the largest), N ragged against the 64-query blocks
     X = inputs.mixture(N=1000, n_clusters=4, dim=10, seed=10)
     check(X, 80.0, 256)
+    # D = 64 with k = 256: the register-tiled kernel's buffers exceed shared
+    # memory, the one-candidate-per-lane kernel runs instead
+    X = inputs.mixture(N=700, n_clusters=4, dim=64, seed=15)
+    check(X, 80.0, 256)
 
 
 def test_recompute_and_bitwise_determinism():
