@@ -187,6 +187,166 @@ knn_kernel(const float* __restrict__ X, int64_t N, int D, int k, int64_t q0, int
     }
 }
 
+// ---- register-tiled kNN over the transposed data ----
+//
+// Xt is D x Np (Np = N rounded up to kTileC, zero past N). A CTA owns kTileQ
+// queries; 128-candidate tiles stream through a double-buffered shared
+// buffer by 16-byte cp.async. Thread (ty, tx) of the 16 x 16 grid holds the
+// 4 x 8 distances of queries 4 ty .. 4 ty + 3 and candidates 4 tx .. 4 tx + 3,
+// 64 + 4 tx .. 64 + 4 tx + 3, accumulated over d in order (the same sums as
+// knn_kernel). The tile of distances goes to shared memory; warp w then
+// filters queries 8 w .. 8 w + 7 against their current k-th entry and
+// inserts the survivors into the sorted lists.
+constexpr int kTileQ = 64;
+constexpr int kTileC = 128;
+constexpr int kTiledThreads = 256;
+constexpr int kDistStride = kTileC + 4;
+
+__host__ __forceinline__ size_t knn_tiled_smem_bytes(int D, int k) {
+    return sizeof(float) * ((size_t)D * kTileQ + 2 * (size_t)D * kTileC + (size_t)kTileQ * kDistStride) +
+           (sizeof(float) + sizeof(int)) * (size_t)kTileQ * k;
+}
+
+__global__ void transpose_pad_kernel(const float* __restrict__ X, int64_t N, int D, int64_t Np,
+                                     float* __restrict__ Xt) {
+    const int64_t total = (int64_t)D * Np;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = e / Np, n = e - d * Np;
+        Xt[e] = n < N ? X[n * D + d] : 0.0f;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
+// copies rows d = 0..D-1 of Xt[:, n0 .. n0 + W) into dst[d][0 .. W) (W floats per row)
+template <int W>
+__device__ __forceinline__ void load_cols(float* dst, const float* __restrict__ Xt, int64_t Np, int D,
+                                          int64_t n0) {
+    constexpr int V = W / 4;  // float4 per row
+    for (int t = threadIdx.x; t < D * V; t += kTiledThreads) {
+        const int d = t / V, v = t - d * V;
+        cp_async16(dst + d * W + 4 * v, Xt + (int64_t)d * Np + n0 + 4 * v);
+    }
+}
+
+__global__ void __launch_bounds__(kTiledThreads, 1)
+knn_tiled_kernel(const float* __restrict__ Xt, int64_t N, int64_t Np, int D, int k,
+                 int32_t* __restrict__ out_idx, float* __restrict__ out_d2) {
+    extern __shared__ __align__(16) float sm_t[];
+    float* s_q = sm_t;                                // [D][kTileQ]
+    float* s_c = s_q + D * kTileQ;                    // [2][D][kTileC]
+    float* s_d = s_c + 2 * D * kTileC;                // [kTileQ][kDistStride]
+    float* s_ld = s_d + kTileQ * kDistStride;         // [kTileQ][k]
+    int* s_li = reinterpret_cast<int*>(s_ld + kTileQ * k);
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t nqb = (N + kTileQ - 1) / kTileQ;
+    const int64_t ntiles = Np / kTileC;
+    for (int64_t qb = blockIdx.x; qb < nqb; qb += gridDim.x) {
+        const int64_t q0 = qb * kTileQ;
+        __syncthreads();  // the previous block's lists are written out
+        for (int t = threadIdx.x; t < kTileQ * k; t += kTiledThreads) {
+            s_ld[t] = INFINITY;
+            s_li[t] = INT_MAX;
+        }
+        float thr[8];
+        int thi[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) { thr[u] = INFINITY; thi[u] = INT_MAX; }
+        load_cols<kTileQ>(s_q, Xt, Np, D, q0);
+        load_cols<kTileC>(s_c, Xt, Np, D, 0);
+        cp_async_commit();
+        for (int64_t tile = 0; tile < ntiles; ++tile) {
+            const int b = (int)(tile & 1);
+            if (tile + 1 < ntiles) load_cols<kTileC>(s_c + (b ^ 1) * D * kTileC, Xt, Np, D, (tile + 1) * kTileC);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            // 4 x 8 distances of this thread
+            float acc[4][8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+            const float* cb = s_c + b * D * kTileC;
+#pragma unroll 2
+            for (int d = 0; d < D; ++d) {
+                const float4 a = *reinterpret_cast<const float4*>(s_q + d * kTileQ + 4 * ty);
+                const float4 c0 = *reinterpret_cast<const float4*>(cb + d * kTileC + 4 * tx);
+                const float4 c1 = *reinterpret_cast<const float4*>(cb + d * kTileC + 64 + 4 * tx);
+                const float qa[4] = {a.x, a.y, a.z, a.w};
+                const float cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float t = qa[i] - cc[j];
+                        acc[i][j] = fmaf(t, t, acc[i][j]);
+                    }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float* row = s_d + (4 * ty + i) * kDistStride;
+                *reinterpret_cast<float4*>(row + 4 * tx) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                *reinterpret_cast<float4*>(row + 64 + 4 * tx) =
+                    make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+            }
+            __syncthreads();
+            // selection: warp wid owns queries 8 wid .. 8 wid + 7
+            const int64_t c_base = tile * kTileC;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int ql = 8 * wid + u;
+                const int64_t gq = q0 + ql;
+                const float4 v = *reinterpret_cast<const float4*>(s_d + ql * kDistStride + 4 * lane);
+                const float dv[4] = {v.x, v.y, v.z, v.w};
+                float* ld = s_ld + ql * k;
+                int* li = s_li + ql * k;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int64_t gc = c_base + 4 * lane + t;
+                    float dd = dv[t];
+                    // a non-finite distance ranks as +inf (by index among equals)
+                    if (!(dd <= 3.402823466e38f)) dd = INFINITY;
+                    const int ci = (int)gc;
+                    const bool take = gq < N && gc < N && gc != gq && knn_less(dd, ci, thr[u], thi[u]);
+                    unsigned m = __ballot_sync(kFullA, take);
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        const float d = __shfl_sync(kFullA, dd, src);
+                        const int i = __shfl_sync(kFullA, ci, src);
+                        if (knn_less(d, i, thr[u], thi[u])) {
+                            knn_insert(ld, li, k, d, i, lane);
+                            thr[u] = ld[k - 1];
+                            thi[u] = li[k - 1];
+                        }
+                    }
+                }
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+        for (int t = threadIdx.x; t < kTileQ * k; t += kTiledThreads) {
+            const int q = t / k, m = t - q * k;
+            const int64_t gq = q0 + q;
+            if (gq < N) {
+                out_idx[gq * k + m] = s_li[t];
+                out_d2[gq * k + m] = s_ld[t];
+            }
+        }
+    }
+}
+
 // Bisection on beta per row (warp per row), FP64, the oracle's rule; writes
 // p_{j|i} (FP64) over the row's k neighbours.
 __global__ void calibrate_kernel(const float* __restrict__ d2, int64_t N, int k, double target,
@@ -522,6 +682,10 @@ struct tsne_affinity {
     int D = 0, k = 0;
     int sm_count = 0;
     cudaStream_t stream = nullptr;
+    int max_smem = 0;             // opt-in shared memory per block
+    bool tiled = false;           // knn_tiled_kernel fits (else knn_kernel)
+    int64_t Np = 0;               // N rounded up to the candidate tile
+    float* Xt = nullptr;          // [D][Np] transposed, zero-padded X
     int32_t* knn_idx = nullptr;   // [N k]
     float* knn_d2 = nullptr;      // [N k]
     double* pc = nullptr;         // [N k] p_{j|i}
@@ -551,7 +715,7 @@ int aff_cuda_fail(cudaError_t e, const char* what) {
 
 void free_affinity(tsne_affinity* a) {
     if (!a) return;
-    void* ps[] = {a->knn_idx, a->knn_d2, a->pc, a->keys[0], a->keys[1], a->items[0], a->items[1],
+    void* ps[] = {a->Xt, a->knn_idx, a->knn_d2, a->pc, a->keys[0], a->keys[1], a->items[0], a->items[1],
                   a->counts, a->in_ptr, a->row_ptr, a->col, a->val};
     for (void* p : ps)
         if (p) cudaFree(p);
@@ -597,10 +761,14 @@ int tsne_affinity_create(int64_t N, int32_t D, int32_t k, void* stream, tsne_aff
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&a->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&a->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     for (int e = 0; e < 5 && ce == cudaSuccess; ++e) ce = cudaEventCreate(&a->ev[e]);
     if (ce != cudaSuccess) { free_affinity(a); return aff_cuda_fail(ce, "device setup"); }
     const int64_t nblocks = (nk + fitsne::kRadixTile - 1) / fitsne::kRadixTile;
+    a->tiled = fitsne::knn_tiled_smem_bytes(D, k) <= (size_t)a->max_smem;
+    a->Np = (N + fitsne::kTileC - 1) / fitsne::kTileC * fitsne::kTileC;
     int rc = TSNE_OK;
+    if (a->tiled) rc = aff_alloc(&a->Xt, (size_t)D * (size_t)a->Np, "transposed X");
     if (!rc) rc = aff_alloc(&a->knn_idx, (size_t)nk, "kNN indices");
     if (!rc) rc = aff_alloc(&a->knn_d2, (size_t)nk, "kNN distances");
     if (!rc) rc = aff_alloc(&a->pc, (size_t)nk, "conditional affinities");
@@ -639,7 +807,19 @@ int tsne_affinity_compute(tsne_affinity* a, const float* X, double perplexity, t
     a->nnz = -1;
     ACU(cudaEventRecord(a->ev[0], st), "event");
     // 1. exact kNN
-    {
+    if (a->tiled) {
+        const int64_t total = (int64_t)a->D * a->Np;
+        transpose_pad_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 8LL * a->sm_count), 256, 0, st>>>(
+            X, N, a->D, a->Np, a->Xt);
+        const int64_t nqb = (N + kTileQ - 1) / kTileQ;
+        const size_t smem = knn_tiled_smem_bytes(a->D, k);
+        ACU(cudaFuncSetAttribute(knn_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "kNN shared memory");
+        knn_tiled_kernel<<<(int)std::min<int64_t>(nqb, 1 << 20), kTiledThreads, smem, st>>>(
+            a->Xt, N, a->Np, a->D, k, a->knn_idx, a->knn_d2);
+        ACU(cudaGetLastError(), "kNN launch");
+        a->launches += 1;  // the transpose (the kNN kernel is counted below)
+    } else {
         const int64_t nqb = (N + kKnnWarps * kKnnQ - 1) / (kKnnWarps * kKnnQ);
         const int grid = (int)std::min<int64_t>(nqb, 64LL * a->sm_count);
         // a per-function attribute: set for this workspace's size at each launch

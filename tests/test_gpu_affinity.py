@@ -8,7 +8,8 @@ bounded:
     (FP32, difference form) agree with the oracle's (FP64) to 1e-5 relative;
   - the neighbour lists agree exactly except where two candidates' FP64
     distances are within that tolerance of each other (a near-tie that FP32
-    may order either way); on integer-valued data every distance is exact
+    may order either way: each differing row must hold such a pair among the
+    oracle's k + 1 nearest); on integer-valued data every distance is exact
     in both precisions and the lists, ties included, agree bit for bit;
   - the CSR structure (row_ptr, col) is equal wherever no near-tie touches
     the row or column;
@@ -69,10 +70,18 @@ def check(X, perplexity, k, expect_exact_lists=False):
     idx_o, d2_o = oaff.exact_knn(X, k)
     # sorted distances: unique
     assert np.allclose(d2_g, d2_o, rtol=RTOL_D2, atol=1e-30)
-    bad = near_tie_rows(X, idx_g, idx_o, d2_o)
+    order_bad = near_tie_rows(X, idx_g, idx_o, d2_o)
     if expect_exact_lists:
-        assert not bad
-    assert len(bad) <= max(2, N // 200)
+        assert not order_bad
+    # FP32 can reorder two neighbours only where their FP64 distances lie
+    # within its rounding: every differing row has such a pair among the
+    # oracle's k + 1 nearest
+    _, d2_more = oaff.exact_knn(X, min(k + 1, N - 1))
+    close = (np.diff(d2_more, axis=1) <= RTOL_D2 * d2_more[:, 1:]).any(axis=1)
+    assert all(close[i] for i in order_bad), sorted(i for i in order_bad if not close[i])
+    # P depends on the neighbour sets only; rows whose sets differ (a near-tie at
+    # the k-th place) are left out of the comparison below with their columns
+    bad = {i for i in order_bad if set(idx_g[i].tolist()) != set(idx_o[i].tolist())}
     # calibration reached on every row where it can be (more exact ties at the
     # smallest distance than the perplexity allows make it unreachable: the
     # oracle's own bisection then ends after 200 steps, and so must the GPU's)
@@ -84,7 +93,7 @@ def check(X, perplexity, k, expect_exact_lists=False):
     assert ok.mean() > 0.9
     assert np.all(np.abs(entropy(pc)[ok] - np.log(perplexity)) < 1.1e-5)
     same = np.ones(N, bool)
-    same[list(bad)] = False
+    same[list(order_bad)] = False
     assert np.allclose(pc[~ok & same], pc_o[~ok & same], rtol=RTOL_P, atol=1e-12)
     assert np.allclose(pc.sum(axis=1), 1.0, rtol=0, atol=1e-12)
     # structure and values
