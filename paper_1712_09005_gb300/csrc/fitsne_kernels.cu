@@ -664,13 +664,15 @@ __device__ __forceinline__ void attract(float yi0, float yi1, int j, float v,
 // Rows are taken kRowLanes lanes at a time (32 / kRowLanes rows per warp
 // step; 32 measured fastest on GB300). Entries of one row [beg, end) are
 // shared out over its lanes in windows of 4 kRowLanes: lane g of the row's
-// group takes entries beg + 4 kRowLanes w + 4 g + q (q = 0..3, those below
-// end) of window w = 0, 1, ... in that order, and the group's partial sums
-// are combined by an xor tree over its lanes. The order depends only on the
-// row's own entries (not on where the row sits in memory), so every force
-// kernel, and a relabelled copy of P whose rows keep their entry order, give
-// bitwise equal row sums. RowBuf holds the first W windows of a lane's row,
-// loaded ahead of use.
+// group takes entries beg + 4 kRowLanes w + kRowLanes q + g (q = 0..3, those
+// below end) of window w = 0, 1, ... in that order, and the group's partial
+// sums are combined by an xor tree over its lanes. Each load of col and val
+// is then one contiguous run of kRowLanes entries (a lane stride of 4 bytes,
+// about 5 sectors per 32 entries, where a stride of 16 bytes touched 16).
+// The order depends only on the row's own entries (not on where the row sits
+// in memory), so every force kernel, and a relabelled copy of P whose rows
+// keep their entry order, give bitwise equal row sums. RowBuf holds the first
+// W windows of a lane's row, loaded ahead of use.
 #ifndef FITSNE_ROW_LANES
 #define FITSNE_ROW_LANES 32
 #endif
@@ -681,7 +683,8 @@ template <int W>
 struct RowBuf {
     int c[4 * W];
     float v[4 * W];
-    int beg, end;
+    int base;  // beg + g: this lane's first entry
+    int rem;   // end - base: the lane takes offsets 4 kRowLanes w + kRowLanes q below rem
 };
 
 // Masked streaming loads of the first W windows of a row; g: the lane's
@@ -689,16 +692,18 @@ struct RowBuf {
 template <int W>
 __device__ __forceinline__ void row_load(RowBuf<W>& b, const int32_t* __restrict__ col,
                                          const float* __restrict__ val, int beg, int end, int g) {
-    b.beg = beg;
-    b.end = end;
+    b.base = beg + g;
+    b.rem = end - b.base;
+    const int32_t* __restrict__ cp = col + b.base;
+    const float* __restrict__ vp = val + b.base;
 #pragma unroll
     for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int e = beg + 4 * kRowLanes * w + 4 * g + q;
-            const bool in = e < end;
-            b.c[4 * w + q] = in ? __ldcs(&col[e]) : 0;
-            b.v[4 * w + q] = in ? __ldcs(&val[e]) : 0.0f;
+            const int off = 4 * kRowLanes * w + kRowLanes * q;
+            const bool in = off < b.rem;
+            b.c[4 * w + q] = in ? __ldcs(cp + off) : 0;
+            b.v[4 * w + q] = in ? __ldcs(vp + off) : 0.0f;
         }
 }
 
@@ -708,30 +713,30 @@ template <int S, int W>
 __device__ __forceinline__ void row_attract(const RowBuf<W>& b, const int32_t* __restrict__ col,
                                             const float* __restrict__ val,
                                             const float* __restrict__ Y, float yi0, float yi1,
-                                            int g, float& a0, float& a1) {
+                                            float& a0, float& a1) {
     a0 = 0.0f;
     a1 = 0.0f;
 #pragma unroll
     for (int w = 0; w < W; ++w)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = b.beg + 4 * kRowLanes * w + 4 * g + q;
-            if (e < b.end) attract<S>(yi0, yi1, b.c[4 * w + q], b.v[4 * w + q], Y, a0, a1);
-        }
+        for (int q = 0; q < 4; ++q)
+            if (4 * kRowLanes * w + kRowLanes * q < b.rem)
+                attract<S>(yi0, yi1, b.c[4 * w + q], b.v[4 * w + q], Y, a0, a1);
+    const int32_t* __restrict__ cp = col + b.base;
+    const float* __restrict__ vp = val + b.base;
 #pragma unroll 2
-    for (int wb = b.beg + 4 * kRowLanes * W; wb < b.end; wb += 4 * kRowLanes) {
+    for (int wb = 4 * kRowLanes * W; wb < b.rem; wb += 4 * kRowLanes) {
         int c[4];
         float v[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int e = wb + 4 * g + q;
-            const bool in = e < b.end;
-            c[q] = in ? __ldcs(&col[e]) : 0;
-            v[q] = in ? __ldcs(&val[e]) : 0.0f;
+            const bool in = wb + kRowLanes * q < b.rem;
+            c[q] = in ? __ldcs(cp + wb + kRowLanes * q) : 0;
+            v[q] = in ? __ldcs(vp + wb + kRowLanes * q) : 0.0f;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (wb + 4 * g + q < b.end) attract<S>(yi0, yi1, c[q], v[q], Y, a0, a1);
+            if (wb + kRowLanes * q < b.rem) attract<S>(yi0, yi1, c[q], v[q], Y, a0, a1);
     }
 }
 
@@ -844,7 +849,7 @@ __device__ __forceinline__ void force_block(const Job& J, const Params* __restri
                 const int rs = r < nrows ? r : 0;
                 const float y0 = __shfl_sync(kFull, yi0, rs), y1 = __shfl_sync(kFull, yi1, rs);
                 float a0, a1;
-                row_attract<S, W>(buf[d], col, val, Y, y0, y1, g, a0, a1);
+                row_attract<S, W>(buf[d], col, val, Y, y0, y1, a0, a1);
                 a0 = group_sum(a0);
                 if (S == 2) a1 = group_sum(a1);
                 const int from = (lane - st * RPW) * kRowLanes;  // group of this lane's row
