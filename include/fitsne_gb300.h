@@ -405,7 +405,11 @@ void* tsne_batch_stream(const tsne_batch* batch);
  * tsne_affinity_create: workspace for N points of dimension D (1..64) and k
  * neighbours (1..256, k < N, 2 N k < 2^31); all device memory (about
  * 40 N k bytes) is allocated here; work is enqueued on stream (cudaStream_t,
- * NULL = legacy default). INVALID_ARG on bad sizes, OOM.
+ * NULL = legacy default). INVALID_ARG on bad sizes, OOM. The kNN kernel is
+ * chosen here: the register-tiled one for N >= 400,000 where its shared
+ * memory (D, k) fits, else the one-candidate-per-lane one; the environment
+ * variable FITSNE_KNN_KERNEL=tiled or =rows, read at create, overrides the
+ * size rule (both give the same lists and distances, bit for bit).
  * tsne_affinity_compute: X is DEVICE memory, N x D row-major FP32, read
  * only; 1 <= perplexity <= k. Writes into *P_out a CSR that points into the
  * workspace: valid until the next compute or destroy, owned by the

@@ -19,6 +19,7 @@
 // Every step is deterministic.
 #include <limits.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -199,6 +200,13 @@ knn_kernel(const float* __restrict__ X, int64_t N, int D, int k, int64_t q0, int
 // inserts the survivors into the sorted lists.
 constexpr int kTileQ = 64;
 constexpr int kTileC = 128;
+// Smallest N for which the tiled kernel is chosen by default. Its selection
+// (sorted insertions between two barriers, 8 warps per SM) costs about the
+// same per query at any N, while the distances cost O(N) per query, so the
+// row kernel (16 warps per SM hide the insertions) wins on small N.
+#ifndef FITSNE_KNN_TILED_MIN_N
+#define FITSNE_KNN_TILED_MIN_N 400000
+#endif
 constexpr int kTiledThreads = 256;
 constexpr int kDistStride = kTileC + 4;
 
@@ -765,7 +773,15 @@ int tsne_affinity_create(int64_t N, int32_t D, int32_t k, void* stream, tsne_aff
     for (int e = 0; e < 5 && ce == cudaSuccess; ++e) ce = cudaEventCreate(&a->ev[e]);
     if (ce != cudaSuccess) { free_affinity(a); return aff_cuda_fail(ce, "device setup"); }
     const int64_t nblocks = (nk + fitsne::kRadixTile - 1) / fitsne::kRadixTile;
-    a->tiled = fitsne::knn_tiled_smem_bytes(D, k) <= (size_t)a->max_smem;
+    // kernel choice: the tiled kernel where its shared memory fits and N is
+    // large; FITSNE_KNN_KERNEL=tiled|rows in the environment overrides the
+    // size rule (tests and tuning; "tiled" still needs the memory to fit)
+    const bool fits = fitsne::knn_tiled_smem_bytes(D, k) <= (size_t)a->max_smem;
+    a->tiled = fits && N >= FITSNE_KNN_TILED_MIN_N;
+    if (const char* ov = getenv("FITSNE_KNN_KERNEL")) {
+        if (!strcmp(ov, "tiled")) a->tiled = fits;
+        else if (!strcmp(ov, "rows")) a->tiled = false;
+    }
     a->Np = (N + fitsne::kTileC - 1) / fitsne::kTileC * fitsne::kTileC;
     int rc = TSNE_OK;
     if (a->tiled) rc = aff_alloc(&a->Xt, (size_t)D * (size_t)a->Np, "transposed X");

@@ -42,6 +42,14 @@ def _built():
     __graft_entry__.build()
 
 
+@pytest.fixture(params=["tiled", "rows"])
+def knn_kernel(request, monkeypatch):
+    """Both kNN kernels on every case (the library picks by N otherwise:
+    the small cases here would all take the row kernel)."""
+    monkeypatch.setenv("FITSNE_KNN_KERNEL", request.param)
+    return request.param
+
+
 def gpu_affinities(X, perplexity, k):
     N, D = X.shape
     with pkg.Affinity(N, D, k) as aff:
@@ -128,12 +136,12 @@ def check(X, perplexity, k, expect_exact_lists=False):
     (1537, 3, 10.0, 2),     # D not a multiple of 4, small k (30)
     (2000, 64, 50.0, 3),    # D at its maximum, k = 150
 ])
-def test_matches_oracle(N, D, perp, seed):
+def test_matches_oracle(N, D, perp, seed, knn_kernel):
     X = inputs.mixture(N=N, n_clusters=7, dim=D, seed=seed)
     check(X, perp, int(3 * perp))
 
 
-def test_integer_data_with_exact_ties_is_bit_exact_in_structure():
+def test_integer_data_with_exact_ties_is_bit_exact_in_structure(knn_kernel):
     """Small-integer coordinates: every squared distance is an exact integer in
     FP32 and FP64, duplicates give zero distances; the neighbour order
     (distance, then index) must agree exactly."""
@@ -143,7 +151,7 @@ def test_integer_data_with_exact_ties_is_bit_exact_in_structure():
     check(X, 5.0, 15, expect_exact_lists=True)
 
 
-def test_k_is_everyone_else_and_k_at_maximum():
+def test_k_is_everyone_else_and_k_at_maximum(knn_kernel):
     # N = k + 1: every point's list is all other points; P is dense
     X = inputs.mixture(N=91, n_clusters=3, dim=20, seed=9)
     check(X, 30.0, 90)
@@ -151,12 +159,12 @@ def test_k_is_everyone_else_and_k_at_maximum():
     X = inputs.mixture(N=1000, n_clusters=4, dim=10, seed=10)
     check(X, 80.0, 256)
     # D = 64 with k = 256: the register-tiled kernel's buffers exceed shared
-    # memory, the one-candidate-per-lane kernel runs instead
+    # memory, the one-candidate-per-lane kernel runs whatever the override
     X = inputs.mixture(N=700, n_clusters=4, dim=64, seed=15)
     check(X, 80.0, 256)
 
 
-def test_recompute_and_bitwise_determinism():
+def test_recompute_and_bitwise_determinism(knn_kernel):
     X = inputs.mixture(N=2500, n_clusters=5, dim=50, seed=11)
     Xd = torch.as_tensor(X, device="cuda")
     with pkg.Affinity(2500, 50, 90) as aff:
@@ -167,6 +175,19 @@ def test_recompute_and_bitwise_determinism():
         assert np.array_equal(u, v)
     assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1])  # same kNN graph
     assert not np.array_equal(a[2], c[2])
+
+
+def test_tiled_and_row_kernels_agree_bitwise(monkeypatch):
+    """Both kNN kernels sum the same squared differences in the same order of
+    d and sort by (distance, index): the lists, distances and P are equal bit
+    for bit (N ragged against both kernels' tiles)."""
+    X = inputs.mixture(N=3001, n_clusters=6, dim=50, seed=21)
+    out = {}
+    for kern in ("tiled", "rows"):
+        monkeypatch.setenv("FITSNE_KNN_KERNEL", kern)
+        out[kern] = gpu_affinities(X, 30.0, 90)
+    for a, b in zip(out["tiled"], out["rows"]):
+        assert np.array_equal(a, b)
 
 
 def test_rejects_bad_perplexity_and_shape():
