@@ -195,7 +195,7 @@ int tsne_run(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
  *
  * Locality relabelling: at iteration relabel_first and every relabel_every
  * iterations after it (plan options), a run relabels its points along a
- * Morton curve of the current embedding (ties by label: deterministic) and
+ * Hilbert curve of the current embedding (ties by label: deterministic) and
  * builds the correspondingly relabelled copy of P (plan-owned, allocated on
  * first use: 8 bytes per stored entry), so that the attraction's reads of
  * neighbouring y_j hit nearby memory (cache reuse). The gradient is unchanged up to

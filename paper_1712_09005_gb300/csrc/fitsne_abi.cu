@@ -646,7 +646,7 @@ static int relabel(tsne_plan* plan, const tsne_csr& P, float* cur, float* nxt) {
         if (int rc = dalloc(&plan->val2, P.nnz, "relabelled val")) return rc;
         plan->nnz2_cap = P.nnz;
     }
-    // the box of the current Y (the Morton keys are taken on it)
+    // the box of the current Y (the curve keys are taken on it)
     CU(fitsne::launch_box(plan->d_job, plan->caps, plan->tables, 0, plan->stream), "box kernel launch");
     plan->launches += 1;
     CU(fitsne::launch_relabel(plan, P, cur, plan->uY_run, plan->gains_run, nxt), "relabel launch");
