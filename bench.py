@@ -9,7 +9,7 @@ region is the whole 1000-iteration job of the N = 1,000,000, s = 2 workload
 first on a scratch copy of the same job.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload n1m_2d|n1m_1d|n100k_2d|n2k_2d|served|affinity]
+                  [--workload n1m_2d|n1m_1d|n100k_2d|n2k_2d|served|affinity|heatmap]
 
 The same JSON line also carries two sub-measurements of the batched forms:
   "batched": 64 independent jobs (N log-uniform in [1k, 200k], s = 2, 1000
@@ -24,6 +24,9 @@ The same JSON line also carries two sub-measurements of the batched forms:
              --workload served runs the whole 500-job stream instead.
 --workload affinity times the GPU construction of P itself (exact kNN,
 bandwidths, symmetrisation) for the N = 1M, D = 50 mixture.
+--workload heatmap times the t-SNE heatmaps of Sec. 5 (bins of a 1-D
+embedding, gene x bin sums, nearest genes) on a synthetic 50,000-cell x
+25,000-gene count matrix.
 
 Under torchrun each rank runs its own independent job (its own seed): the
 method shards by job with no data-path exchange, so scaling is weak and
@@ -618,6 +621,105 @@ def run_affinity(a):
     return 0
 
 
+def run_heatmap(a):
+    """--workload heatmap: t-SNE heatmaps (Sec. 5) of N = 50,000 cells and
+    G = 25,000 genes (synthetic counts, ~940 expressed genes per cell, a
+    clustered 1-D layout), 100 bins, the nearest 4 genes of 3 genes of
+    interest (the paper's example). One step = bin + gene x bin sums +
+    nearest genes. The roofline line is the binning kernel's: it streams the
+    expression CSR once (8 bytes per entry, plus y and row_ptr) and writes H
+    (n_bins x G FP64)."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1712_09005_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1712_09005_gb300 as pkg
+    from paper_1712_09005_gb300 import inputs
+    N = a.n or 50_000
+    G, n_bins, goi, m = 25_000, 100, [11, 12_345, 24_999], 4
+    e = inputs.expression(N, G, mean_genes=1000, n_clusters=20, seed=5000)
+    nnz = int(e.row_ptr[-1])
+    E = pkg.DeviceCSR.from_host(*e.as_tuple())
+    yd = torch.as_tensor(e.y, device="cuda")
+    stream = torch.cuda.current_stream()
+    warm, steps = max(3, a.warmup), a.steps
+    with pkg.Heatmap(n_bins, G, max_goi=len(goi)) as hm:
+        H = torch.empty((n_bins, G), dtype=torch.float64, device="cuda")
+        for _ in range(warm):
+            hm.bin(yd, E, H)
+            hm.nearest(H, goi, m)
+        launches0 = hm.launch_count()
+        sampler = ClockSampler(local)
+        sampler.start()
+        torch.cuda.synchronize()
+        phases = []
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            hm.bin(yd, E, H)  # synchronises (error flags)
+            hm.nearest(H, goi, m)
+            phases.append(hm.phase_ms())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = ev0.elapsed_time(ev1) / steps
+        launches = hm.launch_count() - launches0
+        # end to end: y and E from pinned host memory, H and the gene lists back
+        yh = torch.from_numpy(e.y).pin_memory()
+        rph = torch.from_numpy(e.row_ptr).pin_memory()
+        colh = torch.from_numpy(e.col).pin_memory()
+        valh = torch.from_numpy(e.val).pin_memory()
+        Hh = torch.empty((n_bins, G), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            yd.copy_(yh, non_blocking=True)
+            E.row_ptr.copy_(rph, non_blocking=True)
+            E.col.copy_(colh, non_blocking=True)
+            E.val.copy_(valh, non_blocking=True)
+            hm.bin(yd, E, H)
+            idx, dist = hm.nearest(H, goi, m)
+            Hh.copy_(H, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / steps
+    ph = {k: statistics.median(p[k] for p in phases) for k in phases[0]}
+    bytes_bin = 8 * nnz + 4 * (N + 1) + 4 * N + 8 * n_bins * G
+    achieved = bytes_bin / (ph["bin_sums"] * 1e-3) / 1e9
+    peak, peak_kind = peak_hbm()
+    cpu = None
+    if not a.no_cpu_baseline:
+        from oracle import heatmap as ohm
+        t0 = time.perf_counter()
+        Ho, _ = ohm.gene_bin_sums(e.y, e.row_ptr, e.col, e.val, G, n_bins)
+        ohm.nearest(Ho, goi, m)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "builds/s", "cores": 1, "kind": "oracle",
+               "sample": f"one whole build of this workload by the numpy oracle, {dt:.1f} s"}
+    line = {"metric": f"t-SNE heatmap builds/s (N={N} cells, G={G} genes, {n_bins} bins, "
+                      f"{len(goi)} genes of interest x {m} nearest)",
+            "value": 1e3 / ms, "unit": "builds/s", "n_gpus": 1, "steps": steps, "warmup": warm,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (bins), f64 (sums, distances)", "data": "synthetic",
+            "config": {"workload": f"N={N} cells x G={G} genes synthetic counts (nnz {nnz}), "
+                                   f"20-cluster 1-D layout, {n_bins} equal-width bins",
+                       "l2": "expression CSR (%.2f GB) larger than L2, streamed every step" % (8 * nnz / 1e9)},
+            "phases_ms": ph,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "hm_bin_kernel",
+                         "algorithmic_bytes_per_launch": bytes_bin, "peak_source": f"{peak_kind} hbm_gbs"},
+            "e2e": {"value": 1.0 / e2e_s, "unit": "builds/s",
+                    "h2d_bytes_per_step": 4 * N + 4 * (N + 1) + 8 * nnz,
+                    "d2h_bytes_per_step": 8 * n_bins * G + 12 * len(goi) * m},
+            "gpu_launches": launches, "cpu_baseline": cpu, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -625,7 +727,8 @@ def main():
                     help="timed steps [1000 iterations; 3 builds for --workload affinity]")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served", "affinity"], default="n1m_2d")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served", "affinity", "heatmap"],
+                    default="n1m_2d")
     ap.add_argument("--n", type=int, default=0, help="override the workload's N (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -641,13 +744,15 @@ def main():
                     help="seconds of oracle iterations the reference arm times")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = 3 if a.workload == "affinity" else 1000
+        a.steps = {"affinity": 3, "heatmap": 20}.get(a.workload, 1000)
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "served":
         return run_served_only(a)
     if a.workload == "affinity":
         return run_affinity(a)
+    if a.workload == "heatmap":
+        return run_heatmap(a)
     return run_ours(a)
 
 

@@ -432,6 +432,50 @@ int tsne_affinity_phase_ms(const tsne_affinity* aff, double* ms_out);
 int64_t tsne_affinity_launch_count(const tsne_affinity* aff);
 
 /*
+ * t-SNE heatmaps (Sec. 5). A 1-D embedding y of N cells is cut into n_bins
+ * equal-width bins over [min y, max y]:
+ *   w = (max y - min y) / n_bins,  bin(y) = floor((y - min y) * (1 / w)),
+ * each operation rounded once in FP32 (round to nearest, no FMA), clamped to
+ * [0, n_bins - 1]; w = 0 (or 1 / w not finite) puts every cell in bin 0.
+ * Gene g becomes h_g in R^{n_bins}, h_g[b] = sum of E[i, g] over the cells i
+ * of bin b, and genes are compared by |h_g - h_g'| (Euclidean); each gene
+ * of interest is enriched with the m genes nearest to it (itself excluded,
+ * ties by the smaller gene index), the rows of the heatmap.
+ *
+ * tsne_heatmap_create: workspace for n_bins (1..2^20) bins, G genes and up
+ * to max_goi (1..65535) genes of interest per search (about 8 max_goi G
+ * bytes of device memory, allocated here); work is enqueued on stream
+ * (cudaStream_t, NULL = legacy default). INVALID_ARG on bad sizes, OOM.
+ * tsne_heatmap_bin: y is DEVICE fp32 [N] (1 <= N <= 2^31 - 2); E is the
+ * cells x genes expression matrix as a DEVICE CSR (int32 row_ptr[N + 1],
+ * int32 gene index col[nnz] in [0, G), fp32 val[nnz]; nnz < 2^31). Writes
+ * the caller's DEVICE buffers H, FP64 n_bins x G row-major (H[b * G + g] =
+ * h_g[b]), and bin_count, int32 [n_bins] (cells per bin). H is summed with
+ * FP64 atomics: its last bits may differ between calls. Synchronises the
+ * stream; NONFINITE if y holds NaN or Inf, INVALID_ARG if a row of E is
+ * malformed (row_ptr decreasing or beyond nnz) or a gene index is out of
+ * range (such rows / entries are skipped, the rest is summed).
+ * tsne_heatmap_nearest: for each of the n_goi (1..max_goi) gene indices in
+ * goi_host (HOST memory), the m (1..min(256, G - 1)) genes nearest to it in
+ * the distance above over the DEVICE matrix H of the last bin call:
+ * idx_host[q * m + r] and dist_host[q * m + r] (HOST, n_goi x m, int32 and
+ * FP64, in increasing distance). Synchronises the stream; INVALID_ARG on bad
+ * sizes or an index outside [0, G).
+ * tsne_heatmap_phase_ms: device time (CUDA events) of the last calls:
+ * ms_out[0] clearing and range, [1] binning and sums, [2] distances,
+ * [3] selection (0 before the first search). INVALID_ARG before a bin call.
+ */
+typedef struct tsne_heatmap tsne_heatmap;
+int tsne_heatmap_create(int32_t n_bins, int32_t G, int32_t max_goi, void* stream, tsne_heatmap** out);
+int tsne_heatmap_destroy(tsne_heatmap* hm);
+int tsne_heatmap_bin(tsne_heatmap* hm, const float* y, int64_t N, tsne_csr E, double* H, int32_t* bin_count);
+int tsne_heatmap_nearest(tsne_heatmap* hm, const double* H, const int32_t* goi_host, int32_t n_goi, int32_t m,
+                         int32_t* idx_host, double* dist_host);
+int tsne_heatmap_phase_ms(const tsne_heatmap* hm, double* ms_out);
+/* Kernels the workspace has launched (host-side count). */
+int64_t tsne_heatmap_launch_count(const tsne_heatmap* hm);
+
+/*
  * KL(P || Q) without any device allocation (the paper has no counterpart;
  * this exists for callers that cannot call cudaMalloc, e.g. a process whose
  * own allocator owns all device memory, or code that must not let

@@ -9,7 +9,7 @@ produced.
 The arithmetic lives in ``fitsne_oracle.c`` (built here with gcc,
 ``-O2 -ffp-contract=off -fopenmp``); this module only marshals numpy arrays.
 ``affinities.py`` holds the oracle's own input-affinity builder (Sec. 1.1,
-Eq. p_ij).
+Eq. p_ij); ``heatmap.py`` the t-SNE heatmaps of Sec. 5.
 
 Parity status of each function (what pins it is in tests/test_oracle_*.py):
   exact_gradient      pinned: finite differences of KL, closed forms, invariants
@@ -19,6 +19,9 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   fft                 pinned: numpy.fft and the direct DFT
   step / run          pinned: special cases (plain gradient descent, gain rule)
   affinities.build_P  pinned: perplexity, symmetry, normalisation, brute force
+  heatmap.bins        pinned: hand-worked bins, the FP32 decision at a bin edge
+  heatmap.gene_bin_sums  pinned: one-hot sparse product, column totals
+  heatmap.nearest     pinned: scipy cdist, a planted tie, brute force
 """
 from __future__ import annotations
 

@@ -29,7 +29,9 @@ __all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destr
            "tsne_batch_set_tuning", "tsne_batch_get_tuning", "tsne_batch_autotune",
            "tsne_batch_launch_count", "tsne_batch_stream", "Affinity", "tsne_affinity_create",
            "tsne_affinity_destroy", "tsne_affinity_compute", "tsne_affinity_knn_copy",
-           "tsne_affinity_phase_ms", "tsne_affinity_launch_count"]
+           "tsne_affinity_phase_ms", "tsne_affinity_launch_count", "Heatmap", "tsne_heatmap_create",
+           "tsne_heatmap_destroy", "tsne_heatmap_bin", "tsne_heatmap_nearest", "tsne_heatmap_phase_ms",
+           "tsne_heatmap_launch_count"]
 
 
 def lib():
@@ -301,6 +303,103 @@ class Affinity:
     def close(self):
         if self._h is not None:
             tsne_affinity_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tsne_heatmap_create(n_bins: int, G: int, max_goi: int = 64, stream: int | None = None) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_void_p()
+    check(lib().tsne_heatmap_create(n_bins, G, max_goi, ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out
+
+
+def tsne_heatmap_destroy(hm) -> None:
+    check(lib().tsne_heatmap_destroy(hm))
+
+
+def tsne_heatmap_bin(hm, y: torch.Tensor, E: "DeviceCSR", H: torch.Tensor, bin_count: torch.Tensor) -> None:
+    if not (y.is_cuda and y.dtype == torch.float32 and y.is_contiguous() and y.dim() == 1):
+        raise TypeError("y must be a contiguous 1-D CUDA float32 tensor")
+    if not (H.is_cuda and H.dtype == torch.float64 and H.is_contiguous()):
+        raise TypeError("H must be a contiguous CUDA float64 tensor")
+    if not (bin_count.is_cuda and bin_count.dtype == torch.int32 and bin_count.is_contiguous()):
+        raise TypeError("bin_count must be a contiguous CUDA int32 tensor")
+    if H.numel() != H.shape[0] * H.shape[-1] or bin_count.numel() != H.shape[0]:
+        raise ValueError("H must be n_bins x G and bin_count n_bins long")
+    if E.row_ptr.numel() != y.numel() + 1:
+        raise ValueError("E must have one row per cell")
+    check(lib().tsne_heatmap_bin(hm, _ptr(y), y.numel(), E.c(), _ptr(H), _ptr(bin_count)))
+
+
+def tsne_heatmap_nearest(hm, H: torch.Tensor, goi: np.ndarray, m: int, idx: np.ndarray, dist: np.ndarray) -> None:
+    goi = np.ascontiguousarray(goi, dtype=np.int32)
+    if idx.dtype != np.int32 or dist.dtype != np.float64 or idx.size < goi.size * m or dist.size < goi.size * m:
+        raise TypeError("idx must be int32 and dist float64, n_goi x m each")
+    check(lib().tsne_heatmap_nearest(hm, _ptr(H), ctypes.c_void_p(goi.ctypes.data), goi.size, m,
+                                     ctypes.c_void_p(idx.ctypes.data), ctypes.c_void_p(dist.ctypes.data)))
+
+
+def tsne_heatmap_phase_ms(hm) -> list[float]:
+    ms = (ctypes.c_double * 4)()
+    check(lib().tsne_heatmap_phase_ms(hm, ms))
+    return list(ms)
+
+
+def tsne_heatmap_launch_count(hm) -> int:
+    return lib().tsne_heatmap_launch_count(hm)
+
+
+class Heatmap:
+    """t-SNE heatmaps (Sec. 5) of a 1-D embedding of N cells and a cells x
+    genes expression matrix E (DeviceCSR over cells, column = gene index):
+    bin() sums every gene's expression per equal-width bin of the embedding
+    (H, n_bins x G, FP64) and counts the cells per bin; nearest() returns, for
+    each gene of interest, the m genes nearest to it in the Euclidean distance
+    of those per-bin vectors (the rows of the heatmap)."""
+
+    def __init__(self, n_bins: int, G: int, max_goi: int = 64, stream: int | None = None):
+        self.n_bins, self.G, self.max_goi = n_bins, G, max_goi
+        self._h = tsne_heatmap_create(n_bins, G, max_goi, stream)
+
+    def bin(self, y: torch.Tensor, E: "DeviceCSR", H: torch.Tensor | None = None):
+        if H is None:
+            H = torch.empty((self.n_bins, self.G), dtype=torch.float64, device=y.device)
+        if H.shape != (self.n_bins, self.G):
+            raise ValueError(f"H must be {self.n_bins} x {self.G}")
+        counts = torch.empty(self.n_bins, dtype=torch.int32, device=y.device)
+        tsne_heatmap_bin(self._h, y, E, H, counts)
+        return H, counts
+
+    def nearest(self, H: torch.Tensor, goi, m: int):
+        goi = np.asarray(goi, dtype=np.int32).ravel()
+        idx = np.empty((goi.size, m), np.int32)
+        dist = np.empty((goi.size, m), np.float64)
+        tsne_heatmap_nearest(self._h, H, goi, m, idx, dist)
+        return idx, dist
+
+    def phase_ms(self) -> dict:
+        """Device time of the last calls' phases (CUDA events on the workspace's stream)."""
+        return dict(zip(("range", "bin_sums", "distances", "selection"), tsne_heatmap_phase_ms(self._h)))
+
+    def launch_count(self) -> int:
+        return tsne_heatmap_launch_count(self._h)
+
+    def close(self):
+        if self._h is not None:
+            tsne_heatmap_destroy(self._h)
             self._h = None
 
     def __enter__(self):

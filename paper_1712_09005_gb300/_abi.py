@@ -141,6 +141,13 @@ _SIGNATURES = [
     ("tsne_affinity_knn_copy", ctypes.c_int, [_P, _P, _P, _P]),
     ("tsne_affinity_phase_ms", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("tsne_affinity_launch_count", ctypes.c_int64, [_P]),
+    ("tsne_heatmap_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
+                                           ctypes.POINTER(_P)]),
+    ("tsne_heatmap_destroy", ctypes.c_int, [_P]),
+    ("tsne_heatmap_bin", ctypes.c_int, [_P, _P, ctypes.c_int64, tsne_csr, _P, _P]),
+    ("tsne_heatmap_nearest", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    ("tsne_heatmap_phase_ms", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    ("tsne_heatmap_launch_count", ctypes.c_int64, [_P]),
 ]
 
 _lock = threading.Lock()

@@ -19,6 +19,10 @@ Workloads (stand-ins shaped like the paper's 50-dimensional PCA inputs of
                                 perplexity, symmetrised p_ij = (p_j|i + p_i|j)/2N
                                 (Sec. 1.1 and Sec. 3), CSR int32/int32/fp32.
   initial_embedding(N, s)       Y0 ~ N(0, 1e-4 I), fp32.
+  expression(N, G, ...)         a cells x genes count matrix (CSR over cells)
+                                and a clustered 1-D layout of the cells, for
+                                the t-SNE heatmaps of Sec. 5 (shaped like a
+                                single-cell RNA-seq count matrix; synthetic).
 
 Random numbers come from numpy's PCG64 with the seed given.
 """
@@ -213,3 +217,54 @@ def mixture_args(workload: int, job: int = 0, N: int | None = None) -> dict:
 def log_uniform_sizes(n_jobs: int, lo: int, hi: int, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_jobs)).astype(np.int64)
+
+
+@dataclass
+class Expression:
+    """Cells x genes counts as CSR over cells (int32 row_ptr, int32 gene
+    index, fp32 count) and a 1-D layout y (fp32) of the cells."""
+    y: np.ndarray
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    G: int
+    label: np.ndarray
+
+    def as_tuple(self):
+        return self.row_ptr, self.col, self.val
+
+
+def expression(N: int, G: int, mean_genes: float = 1000.0, n_clusters: int = 20,
+               markers: int = 25, seed: int = 0) -> Expression:
+    """Synthetic single-cell counts: cluster c of the cells raises the rate
+    of its own `markers` genes 20-fold over log-normal base rates; a cell of
+    cluster c draws Poisson(mean_genes) reads from its cluster's gene
+    distribution (with replacement), and its row holds each distinct gene
+    with its read count. y places cluster c at 10 c + N(0, 1) along a line, in
+    a shuffled cluster order (a 1-D embedding's layout)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    label = rng.integers(0, n_clusters, size=N)
+    order = rng.permutation(n_clusters)
+    y = (10.0 * order[label] + rng.normal(0.0, 1.0, size=N)).astype(np.float32)
+    base = rng.lognormal(0.0, 1.0, size=G)
+    reads = np.clip(rng.poisson(mean_genes, size=N), 1, None)
+    keys = []
+    for c in range(n_clusters):
+        cells = np.nonzero(label == c)[0]
+        if cells.size == 0:
+            continue
+        w = base.copy()
+        w[rng.choice(G, size=min(markers, G), replace=False)] *= 20.0
+        cdf = np.cumsum(w)
+        cdf /= cdf[-1]
+        r = reads[cells]
+        owner = np.repeat(cells, r)
+        gene = np.minimum(np.searchsorted(cdf, rng.random(owner.size), side="right"), G - 1)
+        keys.append(owner.astype(np.int64) * G + gene)
+    keys = np.concatenate(keys) if keys else np.zeros(0, np.int64)
+    uk, cnt = np.unique(keys, return_counts=True)
+    cell = uk // G
+    row_ptr = np.zeros(N + 1, np.int64)
+    np.cumsum(np.bincount(cell, minlength=N), out=row_ptr[1:])
+    return Expression(y, row_ptr.astype(np.int32), (uk % G).astype(np.int32), cnt.astype(np.float32), G,
+                      label)
