@@ -208,6 +208,21 @@ int tsne_run_iters(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params
                    int32_t it_begin, int32_t count);
 
 /*
+ * Checkpoint and resume of a run in pieces (the paper has no counterpart):
+ * between tsne_run_iters calls the state of a run is the caller's Y plus
+ * the plan's uY and gains. tsne_run_state_save copies uY and gains, in the
+ * caller's labels (N x s fp32 each), to HOST buffers and synchronises;
+ * tsne_run_state_load installs such HOST buffers as the run state of a plan
+ * of the same N and s (this one or another, e.g. in a later process), with
+ * no relabelling in effect, and synchronises. Continuing with
+ * tsne_run_iters(it_begin = the next iteration, same P and schedule) gives
+ * the uninterrupted run's Y bit for bit (relabelling changes no result).
+ * INVALID_ARG on NULL buffers; the buffers' sizes are the caller's duty.
+ */
+int tsne_run_state_save(tsne_plan* plan, float* uY_host, float* gains_host);
+int tsne_run_state_load(tsne_plan* plan, const float* uY_host, const float* gains_host);
+
+/*
  * KL(P || Q) = sum_ij p_ij log(p_ij / q_ij) over the stored entries of P
  * (Sec. 1.1), with Z from the interpolation scheme at Y. Per-entry logs in
  * FP32, every sum across entries in FP64. kl_out is a HOST pointer

@@ -20,6 +20,7 @@ from ._abi import TsneError, check
 
 __all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destroy",
            "tsne_plan_set_box", "tsne_gradient", "tsne_step", "tsne_run", "tsne_run_reset", "tsne_run_iters", "tsne_kl",
+           "tsne_run_state_save", "tsne_run_state_load",
            "tsne_run_host", "tsne_validate_csr", "tsne_plan_status", "tsne_plan_info",
            "tsne_debug_copy", "tsne_plan_profile", "tsne_plan_profile_read",
            "tsne_plan_launch_count", "tsne_kl_noalloc", "TsneError", "Batch", "Tuning",
@@ -137,6 +138,19 @@ def tsne_run(plan, P: DeviceCSR, Y, sched: Schedule, want_kl: bool = True):
 
 def tsne_run_reset(plan) -> None:
     check(lib().tsne_run_reset(plan))
+
+
+def tsne_run_state_save(plan, uY: np.ndarray, gains: np.ndarray) -> None:
+    for a in (uY, gains):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise TypeError("uY and gains must be contiguous float32 host arrays")
+    check(lib().tsne_run_state_save(plan, ctypes.c_void_p(uY.ctypes.data), ctypes.c_void_p(gains.ctypes.data)))
+
+
+def tsne_run_state_load(plan, uY: np.ndarray, gains: np.ndarray) -> None:
+    uY = np.ascontiguousarray(uY, np.float32)
+    gains = np.ascontiguousarray(gains, np.float32)
+    check(lib().tsne_run_state_load(plan, ctypes.c_void_p(uY.ctypes.data), ctypes.c_void_p(gains.ctypes.data)))
 
 
 def tsne_run_iters(plan, P: DeviceCSR, Y, sched: Schedule, it_begin: int, count: int) -> None:
@@ -676,6 +690,18 @@ class Plan:
 
     def run_reset(self):
         tsne_run_reset(self.handle)
+
+    def run_state_save(self):
+        """(uY, gains) of the run, N x s float32 host arrays in the caller's labels."""
+        uY = np.empty((self.N, self.s), np.float32)
+        gains = np.empty((self.N, self.s), np.float32)
+        tsne_run_state_save(self.handle, uY, gains)
+        return uY, gains
+
+    def run_state_load(self, uY: np.ndarray, gains: np.ndarray):
+        if np.shape(uY) != (self.N, self.s) or np.shape(gains) != (self.N, self.s):
+            raise ValueError(f"uY and gains must be {self.N} x {self.s}")
+        tsne_run_state_load(self.handle, uY, gains)
 
     def run_iters(self, P: DeviceCSR, Y: torch.Tensor, sched: Schedule, it_begin: int, count: int):
         _vec(Y, self.N, self.s, "Y")

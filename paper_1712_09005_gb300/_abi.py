@@ -97,6 +97,8 @@ _SIGNATURES = [
     ("tsne_run_reset", ctypes.c_int, [_P]),
     ("tsne_run_iters", ctypes.c_int, [_P, tsne_csr, _P, ctypes.POINTER(tsne_step_params),
                                       ctypes.c_int32, ctypes.c_int32]),
+    ("tsne_run_state_save", ctypes.c_int, [_P, _P, _P]),
+    ("tsne_run_state_load", ctypes.c_int, [_P, _P, _P]),
     ("tsne_kl", ctypes.c_int, [_P, tsne_csr, _P, ctypes.POINTER(ctypes.c_double)]),
     ("tsne_run_host", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P,
                                      ctypes.POINTER(tsne_step_params),

@@ -713,6 +713,38 @@ int tsne_run_reset(tsne_plan* plan) {
     return reset_run_state(plan);
 }
 
+// The run state in the caller's labels: a relabelled run's uY and gains are
+// scattered back through the plan's free y_next buffer before the copy.
+int tsne_run_state_save(tsne_plan* plan, float* uY_host, float* gains_host) {
+    if (int rc = check_plan(plan)) return rc;
+    if (!uY_host || !gains_host) return set_error(TSNE_ERR_INVALID_ARG, "NULL host buffer");
+    const size_t bytes = sizeof(float) * (size_t)(plan->N * plan->s);
+    const float* src[2] = {plan->uY_run, plan->gains_run};
+    float* dst[2] = {uY_host, gains_host};
+    for (int k = 0; k < 2; ++k) {
+        const float* from = src[k];
+        if (plan->reordered) {
+            CU(fitsne::launch_to_labels(plan, src[k], 1, plan->y_next), "run state to caller labels");
+            from = plan->y_next;
+        }
+        CU(cudaMemcpyAsync(dst[k], from, bytes, cudaMemcpyDeviceToHost, plan->stream), "run state read-back");
+        CU(cudaStreamSynchronize(plan->stream), "run state synchronise");
+    }
+    return TSNE_OK;
+}
+
+int tsne_run_state_load(tsne_plan* plan, const float* uY_host, const float* gains_host) {
+    if (int rc = check_plan(plan)) return rc;
+    if (!uY_host || !gains_host) return set_error(TSNE_ERR_INVALID_ARG, "NULL host buffer");
+    const size_t bytes = sizeof(float) * (size_t)(plan->N * plan->s);
+    CU(cudaMemcpyAsync(plan->uY_run, uY_host, bytes, cudaMemcpyHostToDevice, plan->stream), "run state upload");
+    CU(cudaMemcpyAsync(plan->gains_run, gains_host, bytes, cudaMemcpyHostToDevice, plan->stream),
+       "run state upload");
+    CU(cudaStreamSynchronize(plan->stream), "run state synchronise");
+    plan->reordered = 0;  // the loaded state is in the caller's labels
+    return TSNE_OK;
+}
+
 int tsne_run_iters(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
                    int32_t it_begin, int32_t count) {
     if (int rc = check_plan(plan)) return rc;

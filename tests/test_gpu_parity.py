@@ -352,6 +352,46 @@ def test_locality_relabelling(s):
 
 
 @pytest.mark.parametrize("s", [1, 2])
+def test_checkpoint_resume_is_bitwise(s):
+    """A run saved after iteration 26 (uY, gains in the caller's labels, after
+    relabellings at 5, 15 and 25) and resumed in a new plan, and in the same
+    plan, ends with the uninterrupted run's Y bit for bit; so does a run saved
+    before any relabelling (iteration 3). The late-exaggeration window and the
+    momentum switch fall after the resume point."""
+    N = 6000
+    P = affinities(N, 13)
+    Y0 = clustered_Y(N, s, 3.0, seed=33)
+    sched = pkg.Schedule(n_iter=60, early_iters=20, mom_switch_iter=30, late_iters=10, late_alpha=4.0)
+    Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+    kw = dict(relabel_first=5, relabel_every=10)
+    with pkg.Plan(N, s, **kw) as plan:
+        Ya = torch.as_tensor(Y0.copy(), device="cuda")
+        plan.run_reset()
+        plan.run_iters(Pd, Ya, sched, 0, 60)
+        ya = Ya.cpu().numpy()
+    for cut in (27, 3):
+        with pkg.Plan(N, s, **kw) as plan:
+            Yb = torch.as_tensor(Y0.copy(), device="cuda")
+            plan.run_reset()
+            plan.run_iters(Pd, Yb, sched, 0, cut)
+            uY, gains = plan.run_state_save()
+            Ymid = Yb.clone()
+            assert np.all(gains > 0) and np.any(uY != 0)
+            plan.run_iters(Pd, Yb, sched, cut, 60 - cut)  # same plan, no save/load
+            assert np.array_equal(Yb.cpu().numpy(), ya)
+            plan.run_state_load(uY, gains)  # same plan, back to the checkpoint
+            Yc = Ymid.clone()
+            plan.run_iters(Pd, Yc, sched, cut, 60 - cut)
+            assert np.array_equal(Yc.cpu().numpy(), ya)
+        with pkg.Plan(N, s, **kw) as plan2:  # a fresh plan
+            plan2.run_state_load(uY, gains)
+            Yd = Ymid.clone()
+            plan2.run_iters(Pd, Yd, sched, cut, 60 - cut)
+            assert plan2.status() == 0
+            assert np.array_equal(Yd.cpu().numpy(), ya)
+
+
+@pytest.mark.parametrize("s", [1, 2])
 def test_force_schedules_agree(s):
     """The force kernel's work schedules (grid-stride chunks, SM-local regions)
     change which warp computes a row, not the arithmetic or its order:
