@@ -99,3 +99,32 @@ def test_null_affinity_is_rejected(lib):
     assert lib.tsne_affinity_compute(None, None, 30.0, ctypes.byref(csr)) == _abi.TSNE_ERR_INVALID_ARG
     assert lib.tsne_affinity_knn_copy(None, None, None, None) == _abi.TSNE_ERR_INVALID_ARG
     assert lib.tsne_affinity_launch_count(None) == 0
+
+
+@pytest.mark.parametrize("n_bins,G,max_goi", [
+    (0, 100, 4),              # no bins
+    ((1 << 20) + 1, 100, 4),  # n_bins above 2^20
+    (10, 0, 4),               # no genes
+    (10, 100, 0),             # no genes of interest
+    (10, 100, 65536),         # max_goi above 65535
+    (1 << 20, 1 << 21, 1),    # n_bins x G above 2^40
+])
+def test_heatmap_create_rejects_bad_arguments(lib, n_bins, G, max_goi):
+    from paper_1712_09005_gb300 import _abi
+    out = ctypes.c_void_p(1)
+    rc = lib.tsne_heatmap_create(n_bins, G, max_goi, None, ctypes.byref(out))
+    assert rc == _abi.TSNE_ERR_INVALID_ARG
+    assert out.value is None
+    assert lib.tsne_last_error_string()
+
+
+def test_null_heatmap_and_run_state_are_rejected(lib):
+    from paper_1712_09005_gb300 import _abi
+    assert lib.tsne_heatmap_destroy(None) == 0
+    assert lib.tsne_heatmap_bin(None, None, 10, _abi.tsne_csr(), None, None) == _abi.TSNE_ERR_INVALID_ARG
+    assert lib.tsne_heatmap_nearest(None, None, None, 1, 1, None, None) == _abi.TSNE_ERR_INVALID_ARG
+    ms = (ctypes.c_double * 4)()
+    assert lib.tsne_heatmap_phase_ms(None, ms) == _abi.TSNE_ERR_INVALID_ARG
+    assert lib.tsne_heatmap_launch_count(None) == 0
+    assert lib.tsne_run_state_save(None, None, None) == _abi.TSNE_ERR_INVALID_ARG
+    assert lib.tsne_run_state_load(None, None, None) == _abi.TSNE_ERR_INVALID_ARG
