@@ -80,6 +80,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(v: float) -> float:
+    """The largest v over the ranks of the process group (v itself alone).
+    The replicas exchange only this scalar (and barriers): no data path."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, N: int, K: int, seconds_max: float) -> float:
+    """Point-iterations/s of the whole job: every rank runs its own N-point job
+    for K iterations (weak scaling), timed by the slowest rank."""
+    return world * N * K / seconds_max
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
 
@@ -217,7 +236,9 @@ def run_reference(a):
     import oracle
     oracle.build()
     num, N, s, fixed, over, desc = WORKLOADS[a.workload]
-    N = a.n or N
+    if a.n:
+        N = a.n
+        desc = f"{desc} [N overridden to {N}]"
     import torch
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     P, Y0 = make_inputs(a.workload, 0, dev, N)
@@ -439,12 +460,8 @@ def run_ours(a):
     status = plan.status()
     if status != 0:
         raise RuntimeError(f"device status {status} after the timed run")
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * N * K / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms)
+    value = whole_job_rate(world, N, K, ms_max / 1e3)
 
     # roofline of the dominant kernel: attraction + interpolation + update
     n = info["n"]
@@ -469,14 +486,10 @@ def run_ours(a):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         plan.run_host(rp.numpy(), cl.numpy(), vl.numpy(), Yh.numpy(), sched_e2e, want_kl=False)
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0)
         h2d = 4 * (N + 1) + 8 * P.nnz + 4 * N * s
         d2h = 4 * N * s
-        e2e = {"value": world * N * K / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+        e2e = {"value": whole_job_rate(world, N, K, dt), "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                "d2h_bytes_per_step": d2h / K,
                "note": "one tsne_run_host call: P and Y0 uploaded once, Y downloaded once; "
                        "bytes per step = call totals / K"}
