@@ -80,7 +80,8 @@ typedef struct {
  *         SM's warps take their own region's blocks first (so, in a
  *         relabelled run, they gather neighbours from one working set that
  *         stays in the SM's L1), then help the regions still in progress;
- * AUTO    REGION (a plan's steps and gradients; batches use GRID). */
+ * AUTO    REGION (a plan's steps and gradients; batches always use REGION
+ *         over all their jobs' rows). */
 #define TSNE_FORCE_AUTO 0
 #define TSNE_FORCE_GRID 1
 #define TSNE_FORCE_REGION 2
