@@ -112,3 +112,22 @@ def test_nearest_planted_and_brute_force():
 def test_rejects_non_finite_embedding():
     with pytest.raises(ValueError):
         ohm.bins(np.array([0.0, np.nan], np.float32), 3)
+
+
+def test_expression_generator_is_a_valid_count_matrix():
+    """The synthetic cells x genes counts: a well-formed CSR (rows in cell
+    order, distinct sorted genes per row, positive integer counts), seeded,
+    with a 1-D layout that keeps each cluster's cells together."""
+    e = inputs.expression(1500, 300, mean_genes=40, n_clusters=5, markers=6, seed=9)
+    assert e.row_ptr[0] == 0 and np.all(np.diff(e.row_ptr) >= 1)
+    assert e.row_ptr[-1] == e.col.size == e.val.size
+    for i in range(e.y.size):
+        c = e.col[e.row_ptr[i]:e.row_ptr[i + 1]]
+        assert np.all(np.diff(c) > 0) and c.min() >= 0 and c.max() < e.G
+    assert np.all(e.val >= 1) and np.all(e.val == np.round(e.val))
+    again = inputs.expression(1500, 300, mean_genes=40, n_clusters=5, markers=6, seed=9)
+    assert np.array_equal(again.col, e.col) and np.array_equal(again.y, e.y)
+    # clusters sit 10 apart with unit spread: each cluster's cells span < 10
+    for c in range(5):
+        yc = e.y[e.label == c]
+        assert yc.max() - yc.min() < 10.0
