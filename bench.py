@@ -243,14 +243,14 @@ def run_reference(a):
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     P, Y0 = make_inputs(a.workload, 0, dev, N)
     sched_args = dict(n_iter=max(1000, a.steps), **over)
-    # warm-up (at most one iteration), then a bounded number of timed iterations
+    # W warm-up iterations, then a bounded number of timed iterations
     if a.warmup > 0:
-        oracle_iterations(P, Y0, a.workload, sched_args, 0.0, 1)
+        oracle_iterations(P, Y0, a.workload, sched_args, 1e9, a.warmup)
     iters, dt, cores = oracle_iterations(P, Y0, a.workload, sched_args, a.ref_budget, a.steps)
     value = N * iters / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
-        "steps": iters, "warmup": min(a.warmup, 1), "ms_per_step": 1e3 * dt / iters,
+        "steps": iters, "warmup": a.warmup, "ms_per_step": 1e3 * dt / iters,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": desc, "N": N, "nnz": int(P.nnz), "s": s,
                                         "iterations": [0, iters]},
@@ -320,14 +320,10 @@ def run_batched_compare(n_jobs: int, n_iter: int):
             kls = [b.kl(j) for j in ids]
         return dt, kls, launches, picked
 
-    # the autotuner's pick (chunk, FFT threads, interval policy), timed
-    t_tuned, kl_tuned, _, tuning = batched_run(None)
-    # the same chunk and FFT threads with the plans' interval rule: the batch then
-    # computes exactly what the loop of plans computes (equal KL, bit for bit)
-    same = pkg.Tuning(tuning.chunk, tuning.fft_threads, pkg._abi.TSNE_NINT_RULE)
-    t_bat, kl_bat, launches_bat, _ = batched_run(same)
+    # the autotuner's pick (chunk, FFT threads; the plans' interval rule):
+    # the batch computes exactly what the loop of plans computes
+    t_bat, kl_bat, launches_bat, tuning = batched_run(None)
     rel = [abs(x - y) / abs(y) for x, y in zip(kl_bat, kl_seq)]
-    rel_tuned = [abs(x - y) / abs(y) for x, y in zip(kl_tuned, kl_seq)]
     sumN = int(sum(P.N for P, _ in jobs))
     return {
         "jobs": n_jobs, "sum_N": sumN, "iterations": n_iter, "s": 2,
@@ -337,13 +333,8 @@ def run_batched_compare(n_jobs: int, n_iter: int):
         "point_iterations_per_s": sumN * n_iter / t_bat,
         "kl_max_rel_diff": max(rel), "kl_mean": float(np.mean(kl_bat)),
         "tuning": {"chunk": tuning.chunk, "fft_threads": tuning.fft_threads,
-                   "n_int_policy": "rule", "autotuner_policy": "fill" if tuning.n_int_policy == 1 else "rule",
-                   "ms_per_iter": tuning.ms_per_iter},
-        "autotuned_run": {"embeddings_per_s": n_jobs / t_tuned, "kl_max_rel_diff": max(rel_tuned),
-                          "kl_mean_rel_diff": float(np.mean(rel_tuned)),
-                          "note": "the tuner's own pick; with the fill policy a job uses more "
-                                  "intervals (same FFT length) than the plans' rule, so its "
-                                  "trajectory differs"},
+                   "n_int_policy": "rule", "ms_per_iter": tuning.ms_per_iter,
+                   "note": "the autotuner's pick, timed after the tuning (its trials excluded)"},
         "gpu_launches_batched": launches_bat, "gpu_launches_sequential": launches_seq,
         "timing": "wall clock around the whole runs, device synchronised",
         "workload": "N log-uniform in [1k, 200k], 10-30-cluster Gaussian mixtures in 50-d, "
@@ -400,6 +391,51 @@ def run_served(n_take: int, n_stream: int = 500):
     }
 
 
+def run_served_saturated(n_take: int):
+    """The served form against a plain one-job-at-a-time loop on the same
+    requests, all present at t = 0 (the server is never idle waiting for
+    arrivals): embeddings/s of both and the jobs' final KL agreement."""
+    import dataclasses
+    import torch
+    import paper_1712_09005_gb300 as pkg
+    from paper_1712_09005_gb300.serve import Server
+    reqs = [dataclasses.replace(r, arrival=0.0) for r in served_requests(n_take)]
+    srv = Server(budget_bytes=40 * 10 ** 9, max_jobs=64, iters_per_round=25)
+    try:
+        out = srv.serve(reqs)
+    finally:
+        srv.close()
+    t_srv = out["makespan_s"]
+    served_Y = {r.rid: r.Y for r in out["results"]}
+    # one job at a time: upload P and Y0, create the job's plan, run it, read Y back
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_Y = {}
+    for r in reqs:
+        Pd = pkg.DeviceCSR.from_host(r.row_ptr, r.col, r.val)
+        Y = torch.as_tensor(r.Y0, device="cuda")
+        with pkg.Plan(r.N, r.s) as plan:
+            plan.run(Pd, Y, r.sched, want_kl=False)
+            seq_Y[r.rid] = Y.cpu().numpy()
+    t_seq = time.perf_counter() - t0
+    # final KL of both results of every job (a plan evaluates both)
+    rel = []
+    for r in reqs:
+        Pd = pkg.DeviceCSR.from_host(r.row_ptr, r.col, r.val)
+        with pkg.Plan(r.N, r.s) as plan:
+            k_srv = plan.kl(Pd, torch.as_tensor(served_Y[r.rid], device="cuda"))
+            k_seq = plan.kl(Pd, torch.as_tensor(seq_Y[r.rid], device="cuda"))
+        rel.append(abs(k_srv - k_seq) / abs(k_seq))
+    return {"jobs": len(reqs), "ok": sum(1 for x in out["results"] if x.status == 0),
+            "embeddings_per_s": len(reqs) / t_srv, "sequential_embeddings_per_s": len(reqs) / t_seq,
+            "speedup": t_seq / t_srv, "kl_max_rel_diff": max(rel),
+            "p50_latency_s": out["p50_s"], "p99_latency_s": out["p99_s"],
+            "timing": "wall clock; the server from the first admission to the last result in host "
+                      "memory, the loop from the first upload to the last result in host memory "
+                      "(plan creation, P upload and Y read-back inside both)",
+            "workload": f"the first {len(reqs)} requests of the served stream, all arriving at t = 0"}
+
+
 def run_ours(a):
     import torch
     import paper_1712_09005_gb300 as pkg
@@ -422,7 +458,21 @@ def run_ours(a):
     P, Y0 = make_inputs(a.workload, rank, "cuda", N)
     Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
     stream = torch.cuda.current_stream()
-    plan = pkg.Plan(N, s, n_intervals=fixed, stream=stream.cuda_stream, force_mode=a.force_mode)
+    plan = pkg.Plan(N, s, n_intervals=fixed, stream=stream.cuda_stream, force_mode=a.force_mode,
+                    order_rounds=-1 if a.no_graph_order else a.order_rounds,
+                    relabel_first=a.relabel_first)
+
+    # one-time analysis of P (not per iteration): the graph order the run
+    # starts in and the copy of P in that order, timed and reported as setup
+    order_ms = None
+    if not a.no_graph_order:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.order(Pd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        order_ms = e0.elapsed_time(e1)
 
     # warm-up on a scratch copy of the job
     Yw = torch.as_tensor(Y0.copy(), device="cuda")
@@ -472,8 +522,43 @@ def run_ours(a):
     peak, peak_kind = peak_hbm()
     traffic = force_traffic(s, N)
 
+    # the whole iteration against the same roofline (every kernel of a step):
+    # 8 nnz + 4 (N + 1) + 24 s N + 8 (s + 5) n^s bytes (for s = 2: 56 n^2;
+    # s = 1: 40 n; the grids are written and read once each)
+    bytes_iter = 8 * P.nnz + 4 * (N + 1) + 24 * s * N + 8 * (s + 5) * (n ** s)
+    iter_achieved = bytes_iter / (ms_max / K / 1e3) / 1e9
+
+    # the whole job (iterations 0 .. n_iter - 1 from Y0, embedding
+    # relabellings included) on the same plan, when the timed window is shorter
+    full_job = None
+    if K < n_iter and not a.no_full_job:
+        Yf = torch.as_tensor(Y0.copy(), device="cuda")
+        plan.run_reset()
+        plan.profile(True)
+        plan.profile_read()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        plan.run_iters(Pd, Yf, sched, 0, n_iter)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+        fprof = plan.profile_read()
+        plan.profile(False)
+        finfo = plan.info()
+        if plan.status() != 0:
+            raise RuntimeError("device status after the full job")
+        full_job = {"iterations": [0, n_iter], "value": N * n_iter / (fms / 1e3), "unit": UNIT,
+                    "ms_per_step": fms / n_iter,
+                    "phases_ms_per_iter": {k: v / max(1, fprof["evals"]) for k, v in fprof["ms"].items()},
+                    "final_n_int": finfo["n_int"], "final_fft_len": finfo["fft_len"],
+                    "note": "the same job from Y0 over its whole schedule, CUDA events on the plan's "
+                            "stream; starts in the order prepared before the timed region"}
+        del Yf
+
     # end to end through the C ABI with host buffers (pinned): upload P and
-    # Y0, K iterations, download Y
+    # Y0, K iterations, download Y (the graph order of P is computed inside)
     e2e = None
     if not a.no_e2e:
         rp = torch.from_numpy(P.row_ptr).pin_memory()
@@ -512,6 +597,7 @@ def run_ours(a):
         batched = run_batched_compare(a.batched_jobs, 1000)
     if rank == 0 and world == 1 and not a.no_served:
         served = run_served(a.served_jobs)
+        served["saturated"] = run_served_saturated(a.served_jobs)
 
     if rank == 0:
         line = {
@@ -529,7 +615,16 @@ def run_ours(a):
                          "kernel": "force_kernel (attraction + interpolation + update)",
                          "algorithmic_bytes_per_launch": bytes_force,
                          "peak_source": f"{peak_kind} hbm_gbs"},
+            "iteration_roofline": {"bound": "hbm", "achieved": iter_achieved, "peak": peak,
+                                   "unit": "GB/s", "frac": iter_achieved / peak,
+                                   "algorithmic_bytes_per_step": bytes_iter,
+                                   "note": "every kernel of one step: 8 nnz + 4 (N + 1) + 24 s N + "
+                                           "8 (s + 5) n^s bytes / ms_per_step"},
             "phases_ms_per_iter": {k: v / max(1, prof["evals"]) for k, v in prof["ms"].items()},
+            "setup": {"graph_order_ms": order_ms,
+                      "note": "once per P, before the timed region: the graph order a run starts "
+                              "in and the copy of P in that order (tsne_plan_order)"},
+            "full_job": full_job,
             "gpu_launches": launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -748,6 +843,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--force-mode", type=int, default=0,
                     help="force-kernel schedule: 0 auto, 1 grid, 2 region (profiling)")
+    ap.add_argument("--no-graph-order", action="store_true",
+                    help="runs start in the caller's labels (no graph order of P)")
+    ap.add_argument("--order-rounds", type=int, default=0,
+                    help="averaging rounds of the graph order (0: the library's default)")
+    ap.add_argument("--relabel-first", type=int, default=0,
+                    help="first embedding relabelling (0: the library's default, < 0: never)")
+    ap.add_argument("--no-full-job", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--batched-jobs", type=int, default=64)

@@ -66,12 +66,15 @@ typedef struct {
 /* Plan options; zero-initialised fields take the defaults in brackets. */
 typedef struct {
     int32_t n_min;     /* floor of the interval rule max(n_min, ceil(width)) [50] (Sec. 2.5) */
-    int32_t n_int_max; /* cap of the rule and size of the grids [1000 if s = 1, 400 if s = 2];
-                          p * n_int_max may not exceed 3000 (s = 1) or 1200 (s = 2) */
+    int32_t n_int_max; /* cap of the rule and size of the grids [min(1000, 3000 / p) if s = 1,
+                          min(400, 1200 / p) if s = 2]; p * n_int_max may not exceed 3000
+                          (s = 1) or 1200 (s = 2) */
     void* stream;      /* cudaStream_t for all work; NULL = the legacy default stream */
     int32_t relabel_first; /* iteration of a run's first locality relabelling [100]; < 0: never */
     int32_t relabel_every; /* iterations between later relabellings [300] */
     int32_t force_mode;    /* work schedule of the force kernel, TSNE_FORCE_* [TSNE_FORCE_AUTO] */
+    int32_t order_rounds;  /* averaging rounds of the graph order a run starts in [8], 1..64;
+                              < 0: runs start in the caller's labels (see tsne_run_iters) */
 } tsne_plan_opts;
 
 /* Work schedules of the force kernel (same arithmetic, bitwise equal results):
@@ -194,19 +197,46 @@ int tsne_run(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
  * uY and gains in the plan between calls. tsne_run equals a reset followed
  * by tsne_run_iters(0, sp->n_iter) (and the optional KL).
  *
- * Locality relabelling: at iteration relabel_first and every relabel_every
- * iterations after it (plan options), a run relabels its points along a
- * Hilbert curve of the current embedding (ties by label: deterministic) and
- * builds the correspondingly relabelled copy of P (plan-owned, allocated on
- * first use: 8 bytes per stored entry), so that the attraction's reads of
- * neighbouring y_j hit nearby memory (cache reuse). The gradient is unchanged up to
- * the order of each row's attraction sum; Y is returned in the caller's
+ * Locality relabelling, so that the attraction's reads of neighbouring y_j
+ * hit nearby memory (cache reuse); each builds the correspondingly
+ * relabelled copy of P (plan-owned, allocated on first use: 8 bytes per
+ * stored entry), rows keeping their entry order:
+ *   - at iteration 0 (a run that starts at iteration 0 in the caller's
+ *     labels; plan option order_rounds > 0) the points take the graph order
+ *     of P: two pseudo-random coordinates per point are averaged over the
+ *     point's row of P order_rounds times (z_i <- sum_j p_ij z_j / sum_j
+ *     p_ij; rows without entries keep 0), and the labels follow a Hilbert
+ *     curve over the result (mean +- 3 standard deviations per coordinate,
+ *     1024 cells each), ties by label. Points of one cluster of the kNN
+ *     graph get nearby labels before the embedding has any structure.
+ *     The order is kept for later runs with the same P (same pointers and
+ *     nnz); the copy of P is rebuilt at every run's start unless
+ *     tsne_plan_order prepared it;
+ *   - at iteration relabel_first and every relabel_every iterations after
+ *     it (plan options) the points are relabelled along a Hilbert curve of
+ *     the current embedding (ties by label).
+ * Every relabelling is deterministic and leaves every result bitwise
+ * unchanged (each row's attraction sum keeps its order; the spread, Z and
+ * KL sums do not depend on the labels); Y is returned in the caller's
  * labels. P must stay the same across the tsne_run_iters calls of one run.
-
  */
 int tsne_run_reset(tsne_plan* plan);
 int tsne_run_iters(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp,
                    int32_t it_begin, int32_t count);
+
+/*
+ * Prepares the graph order of P (see tsne_run_iters) and the copy of P in
+ * that order, so that later runs of this plan with the same P (same
+ * pointers and nnz) start without re-reading P: the caller promises that P's
+ * contents do not change until the next tsne_plan_order call (results with
+ * a changed P would use the stale copy). An embedding relabelling of a run
+ * replaces the copy; the next run then rebuilds it. The paper has no
+ * counterpart (a cache-locality analysis of P, like a sparse library's
+ * matrix preprocessing). A relabelled run of the plan that is continued
+ * afterwards (tsne_run_iters) rebuilds its own copy of P first. Enqueued on
+ * the plan's stream. INVALID_ARG if the plan has order_rounds < 0; OOM.
+ */
+int tsne_plan_order(tsne_plan* plan, tsne_csr P);
 
 /*
  * Checkpoint and resume of a run in pieces (the paper has no counterpart):
@@ -225,9 +255,9 @@ int tsne_run_state_load(tsne_plan* plan, const float* uY_host, const float* gain
 
 /*
  * KL(P || Q) = sum_ij p_ij log(p_ij / q_ij) over the stored entries of P
- * (Sec. 1.1), with Z from the interpolation scheme at Y. Per-entry logs in
- * FP32, every sum across entries in FP64. kl_out is a HOST pointer
- * (synchronises).
+ * (Sec. 1.1), with Z from the interpolation scheme at Y. Squared distances,
+ * logarithms and every sum in FP64 (from the FP32 coordinates and values).
+ * kl_out is a HOST pointer (synchronises).
  */
 int tsne_kl(tsne_plan* plan, tsne_csr P, const float* Y, double* kl_out);
 
@@ -314,7 +344,8 @@ typedef struct tsne_batch tsne_batch;
 /* Batch options; tsne_batch_opts_default fills the defaults in brackets. */
 typedef struct {
     int32_t n_min;     /* floor of the interval rule [50] (Sec. 2.5) */
-    int32_t n_int_max; /* cap of the rule and size of every job's grids [1000 if s = 1, 400 if s = 2] */
+    int32_t n_int_max; /* cap of the rule and size of every job's grids [min(1000, 3000 / p) if
+                          s = 1, min(400, 1200 / p) if s = 2] */
     int32_t max_jobs;  /* job slots, 1 .. 256 [64] */
     int32_t use_graph; /* 1: replay one captured CUDA graph per iteration [1]; 0: plain launches */
     void* stream;      /* cudaStream_t for all work (not the legacy default stream);
@@ -392,10 +423,11 @@ int tsne_batch_get_tuning(const tsne_batch* batch, tsne_batch_tuning* out);
 /*
  * Autotuner: times `iters` iterations of the batch's current jobs under
  * candidate tunings (coordinate search over chunk in {32, 64, 128, 256}, then
- * fft_threads in {256, 512, 1024} for s = 2, then TSNE_NINT_FILL, taken when
- * it costs at most 3 % more, since it only adds intervals), restoring every
- * job's state after each trial, so the jobs' results do not depend on the
- * tuning run. Applies the fastest tuning and writes it (with its measured
+ * fft_threads in {256, 512, 1024} for s = 2), restoring every job's state
+ * after each trial, so the jobs' results do not depend on the tuning run.
+ * Neither knob changes a result bit; the interval policy, which does, is
+ * left as the caller set it (TSNE_NINT_FILL changes a run's final KL by up
+ * to about 1 %). Applies the fastest tuning and writes it (with its measured
  * ms_per_iter) to *out (may be NULL). Synchronises; needs at least one job.
  */
 int tsne_batch_autotune(tsne_batch* batch, int32_t iters, tsne_batch_tuning* out);
@@ -506,7 +538,9 @@ int64_t tsne_heatmap_launch_count(const tsne_heatmap* hm);
  * device image (per-block partial sums of at most 1,024 reduction blocks and
  * a completion counter), held by every GPU that loads the library until
  * process exit. The first call on a device looks up that array's address
- * (cudaGetSymbolAddress), so make it before any stream capture. All calls
+ * (cudaGetSymbolAddress), so make it before any stream capture; the address
+ * is kept until process exit, so do not call this entry point on a device
+ * the process has reset with cudaDeviceReset (the array may move). All calls
  * share the array: calls whose work overlaps on the GPU (different streams,
  * or different host threads on one device) race; serialise them.
  * tsne_noalloc_last_error_string describes the last failure of this entry

@@ -20,7 +20,7 @@ from ._abi import TsneError, check
 
 __all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destroy",
            "tsne_plan_set_box", "tsne_gradient", "tsne_step", "tsne_run", "tsne_run_reset", "tsne_run_iters", "tsne_kl",
-           "tsne_run_state_save", "tsne_run_state_load",
+           "tsne_run_state_save", "tsne_run_state_load", "tsne_plan_order",
            "tsne_run_host", "tsne_validate_csr", "tsne_plan_status", "tsne_plan_info",
            "tsne_debug_copy", "tsne_plan_profile", "tsne_plan_profile_read",
            "tsne_plan_launch_count", "tsne_kl_noalloc", "TsneError", "Batch", "Tuning",
@@ -102,10 +102,12 @@ def _vec(t: torch.Tensor, N: int, s: int, name: str):
 
 def tsne_plan_create(N: int, s: int, n_intervals: int = 0, p: int = 3, n_min: int = 0,
                      n_int_max: int = 0, stream: int | None = None, relabel_first: int = 0,
-                     relabel_every: int = 0, force_mode: int = 0) -> ctypes.c_void_p:
+                     relabel_every: int = 0, force_mode: int = 0,
+                     order_rounds: int = 0) -> ctypes.c_void_p:
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    opts = _abi.tsne_plan_opts(n_min, n_int_max, stream, relabel_first, relabel_every, force_mode)
+    opts = _abi.tsne_plan_opts(n_min, n_int_max, stream, relabel_first, relabel_every, force_mode,
+                               order_rounds)
     out = ctypes.c_void_p()
     check(lib().tsne_plan_create(N, s, n_intervals, p, ctypes.byref(opts), ctypes.byref(out)))
     return out
@@ -138,6 +140,10 @@ def tsne_run(plan, P: DeviceCSR, Y, sched: Schedule, want_kl: bool = True):
 
 def tsne_run_reset(plan) -> None:
     check(lib().tsne_run_reset(plan))
+
+
+def tsne_plan_order(plan, P: DeviceCSR) -> None:
+    check(lib().tsne_plan_order(plan, P.c()))
 
 
 def tsne_run_state_save(plan, uY: np.ndarray, gains: np.ndarray) -> None:
@@ -231,7 +237,9 @@ def tsne_kl_noalloc(P: DeviceCSR, Y: torch.Tensor, s: int, Z: float, kl_out: tor
         stream = torch.cuda.current_stream().cuda_stream
     if not (kl_out.is_cuda and kl_out.dtype == torch.float64 and kl_out.numel() >= 1):
         raise TypeError("kl_out must be a float64 CUDA tensor")
-    N = Y.numel() // s
+    N = P.N
+    if s in (1, 2):
+        _vec(Y, N, s, "Y")  # the kernel reads Y[col[e]] for every stored entry of P
     rc = lib().tsne_kl_noalloc(P.c(), _ptr(Y), N, s, float(Z), _ptr(kl_out),
                                ctypes.c_void_p(stream))
     if rc != 0:
@@ -645,10 +653,10 @@ class Plan:
 
     def __init__(self, N: int, s: int, n_intervals: int = 0, p: int = 3, n_min: int = 0,
                  n_int_max: int = 0, stream: int | None = None, relabel_first: int = 0,
-                 relabel_every: int = 0, force_mode: int = 0):
+                 relabel_every: int = 0, force_mode: int = 0, order_rounds: int = 0):
         self.N, self.s = N, s
         self.handle = tsne_plan_create(N, s, n_intervals, p, n_min, n_int_max, stream,
-                                       relabel_first, relabel_every, force_mode)
+                                       relabel_first, relabel_every, force_mode, order_rounds)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -690,6 +698,11 @@ class Plan:
 
     def run_reset(self):
         tsne_run_reset(self.handle)
+
+    def order(self, P: DeviceCSR):
+        if P.N != self.N:
+            raise ValueError(f"P has {P.N} rows, the plan {self.N} points")
+        tsne_plan_order(self.handle, P)
 
     def run_state_save(self):
         """(uY, gains) of the run, N x s float32 host arrays in the caller's labels."""

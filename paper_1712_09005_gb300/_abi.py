@@ -39,7 +39,8 @@ class tsne_csr(ctypes.Structure):
 class tsne_plan_opts(ctypes.Structure):
     _fields_ = [("n_min", ctypes.c_int32), ("n_int_max", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("relabel_first", ctypes.c_int32),
-                ("relabel_every", ctypes.c_int32), ("force_mode", ctypes.c_int32)]
+                ("relabel_every", ctypes.c_int32), ("force_mode", ctypes.c_int32),
+                ("order_rounds", ctypes.c_int32)]
 
 
 class tsne_step_params(ctypes.Structure):
@@ -97,6 +98,7 @@ _SIGNATURES = [
     ("tsne_run_reset", ctypes.c_int, [_P]),
     ("tsne_run_iters", ctypes.c_int, [_P, tsne_csr, _P, ctypes.POINTER(tsne_step_params),
                                       ctypes.c_int32, ctypes.c_int32]),
+    ("tsne_plan_order", ctypes.c_int, [_P, tsne_csr]),
     ("tsne_run_state_save", ctypes.c_int, [_P, _P, _P]),
     ("tsne_run_state_load", ctypes.c_int, [_P, _P, _P]),
     ("tsne_kl", ctypes.c_int, [_P, tsne_csr, _P, ctypes.POINTER(ctypes.c_double)]),

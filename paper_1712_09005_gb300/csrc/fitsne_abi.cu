@@ -307,7 +307,8 @@ void free_plan(tsne_plan* pl) {
                     pl->h_row_ptr, pl->h_col,      pl->h_val,     pl->h_Y,        pl->perm,
                     pl->inv,       pl->perm_next,  pl->inv_next,  pl->row_len,    pl->cur_of,
                     pl->rp2,       pl->col2,       pl->val2,      pl->sort_keys,  pl->scan_bsum,
-                    pl->relabel_ticket, pl->tmp_state, pl->y_cur, pl->region_next};
+                    pl->relabel_ticket, pl->tmp_state, pl->y_cur, pl->region_next,
+                    pl->gperm,     pl->ginv,       pl->order_z,   pl->order_stats};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete pl;
@@ -430,9 +431,9 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     tsne_plan_opts o{};
     if (opts) o = *opts;
     int n_min = o.n_min > 0 ? o.n_min : 50;
-    int n_int_max = o.n_int_max > 0 ? o.n_int_max : (s == 2 ? 400 : 1000);
     // grid limits: 2-D column FFTs keep ten length-L columns in shared memory
     const int n_cap = (s == 2) ? 1200 : 3000;
+    int n_int_max = o.n_int_max > 0 ? o.n_int_max : std::min(s == 2 ? 400 : 1000, n_cap / p);
     if ((int64_t)p * n_int_max > n_cap)
         return set_error(TSNE_ERR_INVALID_ARG, "p * n_int_max = %d exceeds %d nodes per dimension",
                          p * n_int_max, n_cap);
@@ -454,6 +455,11 @@ int tsne_plan_create(int64_t N, int32_t s, int32_t n_intervals, int32_t p,
     pl->relabel_first = o.relabel_first == 0 ? 100 : o.relabel_first;
     pl->relabel_every = o.relabel_every > 0 ? o.relabel_every : 300;
     pl->force_mode = o.force_mode;
+    pl->order_rounds = o.order_rounds == 0 ? 8 : (o.order_rounds < 0 ? 0 : o.order_rounds);
+    if (pl->order_rounds > 64) {
+        free_plan(pl);
+        return set_error(TSNE_ERR_INVALID_ARG, "order_rounds %d exceeds 64", o.order_rounds);
+    }
     if (pl->force_mode < TSNE_FORCE_AUTO || pl->force_mode > TSNE_FORCE_REGION) {
         free_plan(pl);
         return set_error(TSNE_ERR_INVALID_ARG, "unknown force_mode %d", o.force_mode);
@@ -635,17 +641,76 @@ static bool relabel_at(const tsne_plan* plan, int it) {
 
 // Relabels the run at the current state (Y in cur, in the current labels);
 // the new-label Y is gathered through nxt and copied back into cur.
+static int ensure_p2(tsne_plan* plan, int64_t nnz) {
+    if (nnz <= plan->nnz2_cap && plan->col2) return TSNE_OK;
+    if (plan->col2) cudaFree(plan->col2);
+    if (plan->val2) cudaFree(plan->val2);
+    plan->col2 = nullptr;
+    plan->val2 = nullptr;
+    plan->nnz2_cap = 0;
+    plan->p2_holds_gorder = 0;
+    plan->p2_is_run = 0;
+    if (int rc = dalloc(&plan->col2, nnz, "relabelled col")) return rc;
+    if (int rc = dalloc(&plan->val2, nnz, "relabelled val")) return rc;
+    plan->nnz2_cap = nnz;
+    return TSNE_OK;
+}
+
+static bool same_csr(const tsne_csr& a, const tsne_csr& b) {
+    return a.row_ptr == b.row_ptr && a.col == b.col && a.val == b.val && a.nnz == b.nnz;
+}
+
+// Forgets the graph order and the prepared copy (P's contents may have changed).
+static void forget_order(tsne_plan* plan) {
+    plan->gorder_valid = 0;
+    plan->gorder_prepared = 0;
+    plan->p2_holds_gorder = 0;
+}
+
+// Graph order of P in gperm/ginv: computed unless it is already there for the
+// same P (same pointers and nnz; a stale order after an in-place change of P
+// still gives the same results, only the cache locality suffers).
+static int graph_order_of(tsne_plan* plan, const tsne_csr& P, bool recompute) {
+    if (!recompute && plan->gorder_valid && same_csr(plan->gorder_key, P)) return TSNE_OK;
+    const int64_t N = plan->N;
+    if (!plan->gperm)
+        if (int rc = dalloc(&plan->gperm, N, "graph order")) return rc;
+    if (!plan->ginv)
+        if (int rc = dalloc(&plan->ginv, N, "graph order inverse")) return rc;
+    if (!plan->order_z)
+        if (int rc = dalloc(&plan->order_z, 4 * N, "graph order coordinates")) return rc;
+    if (!plan->order_stats)
+        if (int rc = dalloc(&plan->order_stats, 4 * 256 + 2, "graph order statistics")) return rc;
+    forget_order(plan);
+    CU(fitsne::launch_graph_order(plan, P, plan->order_rounds, plan->gperm, plan->ginv),
+       "graph order launch");
+    plan->gorder_valid = 1;
+    plan->gorder_key = P;
+    return TSNE_OK;
+}
+
+// Start of a run (iteration 0, caller's labels): moves the run to the graph
+// order of P; the relabelled copy of P is rebuilt unless tsne_plan_order
+// prepared it for this P and nothing has overwritten it since.
+static int graph_relabel(tsne_plan* plan, const tsne_csr& P, float* cur, float* nxt) {
+    if (int rc = ensure_p2(plan, P.nnz)) return rc;
+    if (int rc = graph_order_of(plan, P, false)) return rc;
+    const bool reuse = plan->gorder_prepared && plan->p2_holds_gorder;
+    CU(fitsne::launch_apply_order(plan, P, plan->gperm, reuse ? 0 : 1, cur, plan->uY_run,
+                                  plan->gains_run, nxt),
+       "graph order relabel");
+    plan->p2_holds_gorder = 1;
+    plan->p2_is_run = 1;
+    CU(cudaMemcpyAsync(cur, nxt, sizeof(float) * plan->N * plan->s, cudaMemcpyDeviceToDevice,
+                       plan->stream),
+       "relabelled Y copy");
+    return TSNE_OK;
+}
+
 static int relabel(tsne_plan* plan, const tsne_csr& P, float* cur, float* nxt) {
-    if (P.nnz > plan->nnz2_cap) {
-        if (plan->col2) cudaFree(plan->col2);
-        if (plan->val2) cudaFree(plan->val2);
-        plan->col2 = nullptr;
-        plan->val2 = nullptr;
-        plan->nnz2_cap = 0;
-        if (int rc = dalloc(&plan->col2, P.nnz, "relabelled col")) return rc;
-        if (int rc = dalloc(&plan->val2, P.nnz, "relabelled val")) return rc;
-        plan->nnz2_cap = P.nnz;
-    }
+    if (int rc = ensure_p2(plan, P.nnz)) return rc;
+    plan->p2_holds_gorder = 0;  // the copy below replaces the graph-ordered one
+    plan->p2_is_run = 1;
     // the box of the current Y (the curve keys are taken on it)
     CU(fitsne::launch_box(plan->d_job, plan->caps, plan->tables, 0, plan->stream), "box kernel launch");
     plan->launches += 1;
@@ -675,6 +740,12 @@ static int run_iters(tsne_plan* plan, const tsne_csr& P, float* Y, const tsne_st
     J.uY = plan->uY_run;
     J.gains = plan->gains_run;
     J.Z_out = nullptr;
+    if (plan->reordered && !plan->p2_is_run) {
+        // a relabelled run continues after tsne_plan_order replaced its copy of P
+        if (int rc = ensure_p2(plan, P.nnz)) return rc;
+        CU(fitsne::launch_order_copy(plan, P, plan->perm, plan->inv), "relabelled copy of P");
+        plan->p2_is_run = 1;
+    }
     auto set_p = [&]() {
         if (plan->reordered) set_csr(plan, tsne_csr{plan->rp2, plan->col2, plan->val2, P.nnz});
         else set_csr(plan, P);
@@ -684,7 +755,11 @@ static int run_iters(tsne_plan* plan, const tsne_csr& P, float* Y, const tsne_st
     if (int rc = upload_job(plan, &d)) return rc;
     int par = 0;
     for (int it = it0; it < it0 + count; ++it) {
-        if (relabel_at(plan, it)) {
+        if (it == 0 && !plan->reordered && plan->order_rounds > 0) {
+            if (int rc = graph_relabel(plan, P, buf[par], buf[par ^ 1])) return rc;
+            set_p();
+            if (int rc = upload_job(plan, nullptr)) return rc;
+        } else if (relabel_at(plan, it)) {
             if (int rc = relabel(plan, P, buf[par], buf[par ^ 1])) return rc;
             set_p();
             if (int rc = upload_job(plan, nullptr)) return rc;
@@ -762,6 +837,20 @@ int tsne_run(tsne_plan* plan, tsne_csr P, float* Y, const tsne_step_params* sp, 
     return run_device(plan, P, Y, sp, kl_out);
 }
 
+int tsne_plan_order(tsne_plan* plan, tsne_csr P) {
+    if (int rc = check_plan(plan)) return rc;
+    if (int rc = check_csr(plan, P)) return rc;
+    if (plan->order_rounds <= 0)
+        return set_error(TSNE_ERR_INVALID_ARG, "the plan was created without a graph order");
+    if (int rc = ensure_p2(plan, P.nnz)) return rc;
+    if (int rc = graph_order_of(plan, P, true)) return rc;
+    CU(fitsne::launch_order_copy(plan, P, plan->gperm, plan->ginv), "graph order copy of P");
+    plan->p2_holds_gorder = 1;
+    plan->gorder_prepared = 1;
+    plan->p2_is_run = 0;  // a relabelled run in progress rebuilds its copy when it continues
+    return TSNE_OK;
+}
+
 int tsne_kl(tsne_plan* plan, tsne_csr P, const float* Y, double* kl_out) {
     if (int rc = check_plan(plan)) return rc;
     if (int rc = check_csr(plan, P)) return rc;
@@ -832,6 +921,7 @@ int tsne_run_host(tsne_plan* plan, const int32_t* row_ptr, const int32_t* col, c
     }
     CU(cudaMemcpyAsync(plan->h_Y, Y, sizeof(float) * N * plan->s, cudaMemcpyHostToDevice, st), "Y upload");
     tsne_csr P{plan->h_row_ptr, plan->h_col, plan->h_val, nnz};
+    forget_order(plan);  // new contents at the same device addresses
     if (int rc = tsne_validate_csr(plan, P)) return rc;
     if (int rc = run_device(plan, P, plan->h_Y, sp, kl_out)) return rc;
     CU(cudaMemcpyAsync(Y, plan->h_Y, sizeof(float) * N * plan->s, cudaMemcpyDeviceToHost, st), "Y download");

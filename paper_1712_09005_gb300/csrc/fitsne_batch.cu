@@ -277,8 +277,8 @@ int tsne_batch_create(int32_t s, int32_t p, const tsne_batch_opts* opts, tsne_ba
     if (max_jobs > fitsne::kMaxJobs)
         return set_error(TSNE_ERR_INVALID_ARG, "max_jobs %d exceeds %d", max_jobs, fitsne::kMaxJobs);
     int n_min = o.n_min > 0 ? o.n_min : 50;
-    const int n_int_max = o.n_int_max > 0 ? o.n_int_max : (s == 2 ? 400 : 1000);
     const int n_cap = (s == 2) ? 1200 : 3000;
+    const int n_int_max = o.n_int_max > 0 ? o.n_int_max : std::min(s == 2 ? 400 : 1000, n_cap / p);
     if ((int64_t)p * n_int_max > n_cap)
         return set_error(TSNE_ERR_INVALID_ARG, "p * n_int_max = %d exceeds %d nodes per dimension",
                          p * n_int_max, n_cap);
@@ -569,9 +569,10 @@ int tsne_batch_autotune(tsne_batch* b, int32_t iters, tsne_batch_tuning* out) {
         *ms /= (float)iters;
         return TSNE_OK;
     };
-    // coordinate search: spread chunk, then FFT threads, then interval policy
+    // coordinate search: spread chunk, then FFT threads. Both change only the
+    // launch shapes, not a result bit; the interval policy changes the
+    // arithmetic (and a run's final KL by about 1 %), so it stays the caller's.
     tsne_batch_tuning best = start;
-    best.n_int_policy = TSNE_NINT_RULE;
     float best_ms = 0.0f;
     rc = trial(best, &best_ms);
     const int chunks[] = {32, 64, 128, 256};
@@ -593,14 +594,6 @@ int tsne_batch_autotune(tsne_batch* b, int32_t iters, tsne_batch_tuning* out) {
             rc = trial(t, &ms);
             if (rc == TSNE_OK && ms < best_ms) { best = t; best_ms = ms; }
         }
-    }
-    if (rc == TSNE_OK) {
-        // more intervals at the same FFT length are taken unless they cost over 3 %
-        tsne_batch_tuning t = best;
-        t.n_int_policy = TSNE_NINT_FILL;
-        float ms = 0.0f;
-        rc = trial(t, &ms);
-        if (rc == TSNE_OK && ms <= 1.03f * best_ms) { best = t; best_ms = std::min(best_ms, ms); }
     }
     int rc2 = tsne_batch_set_tuning(b, rc == TSNE_OK ? &best : &start);
     if (rc == TSNE_OK) rc = rc2;

@@ -247,6 +247,17 @@ struct tsne_plan {
     unsigned* relabel_ticket;  // [1]
     float* tmp_state;        // [N * s]
     float* y_cur;            // [N * s] run state Y in the relabelled order
+    // graph order of a run's start (fitsne_reorder.cu), allocated on first use
+    int order_rounds;        // averaging rounds of the graph order (0: runs start in the caller's labels)
+    int32_t* gperm;          // [N] graph order: new label -> caller's label
+    int32_t* ginv;           // [N] its inverse
+    int gorder_valid;        // gperm/ginv hold the graph order of the P in gorder_key
+    tsne_csr gorder_key;     // pointers and nnz of that P
+    int gorder_prepared;     // tsne_plan_order: runs with that P may reuse rp2/col2/val2
+    int p2_holds_gorder;     // rp2/col2/val2 hold that P in the graph order
+    int p2_is_run;           // rp2/col2/val2 hold the run's P in the run's order (perm/inv)
+    float* order_z;          // [4 N] two float2 coordinate buffers
+    double* order_stats;     // [4 * 256 + 2] block partials, then the key window (4 floats)
     // force kernel scheduling
     int force_mode;          // TSNE_FORCE_* (plan option)
     int n_regions;           // SM id range of the device
@@ -411,6 +422,19 @@ int phase_launches(int s);  // kernels of one iteration (box .. advance)
 // moved in place.
 cudaError_t launch_relabel(tsne_plan* pl, const tsne_csr& P, const float* Y_cur, float* uY_cur,
                            float* gains_cur, float* Y_out);
+// Graph order of P alone (rounds of neighbour averaging of two coordinates,
+// Hilbert keys, sort): perm_out[k] = caller's label of new label k, inv_out
+// its inverse. Uses pl->order_z, order_stats, sort_keys.
+cudaError_t launch_graph_order(tsne_plan* pl, const tsne_csr& P, int rounds, int32_t* perm_out,
+                               int32_t* inv_out);
+// rp2/col2/val2 = P relabelled by (perm, inv), entries of each row in their order.
+cudaError_t launch_order_copy(tsne_plan* pl, const tsne_csr& P, const int32_t* perm,
+                              const int32_t* inv);
+// Moves the run state to the order perm (new label -> caller's label), as
+// launch_relabel does; copy_P = 0 keeps rp2/col2/val2 (they already hold P in
+// that order).
+cudaError_t launch_apply_order(tsne_plan* pl, const tsne_csr& P, const int32_t* perm, int copy_P,
+                               const float* Y_cur, float* uY_cur, float* gains_cur, float* Y_out);
 // to_caller = 1: dst[perm[k]] = src[k]; 0: dst[k] = src[perm[k]].
 cudaError_t launch_to_labels(tsne_plan* pl, const float* src, int to_caller, float* dst);
 // KL reduction with explicit scratch: 2 doubles per block in partial, a

@@ -1034,8 +1034,9 @@ __global__ void advance_kernel(const Job* __restrict__ jobs, int njobs) {
 
 // ----------------------------------------------------------------------------
 // KL(P || Q) = sum p log p + sum p log(1 + d^2) + (sum p) log Z over the stored
-// entries (Sec. 1.1). Per-entry logarithms in FP32, all sums in FP64, reduced
-// in a fixed order (per block, then by the last block).
+// entries (Sec. 1.1). Distances, logarithms and sums in FP64 from the FP32
+// coordinates and values, reduced in a fixed order (per block, then by the
+// last block).
 // ----------------------------------------------------------------------------
 template <int S>
 __global__ void __launch_bounds__(256)
@@ -1059,16 +1060,16 @@ kl_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
             const float p = val[e];
             if (!(p > 0.0f)) continue;
             const int j = col[e];
-            float d2;
+            double d2;
             if (S == 2) {
-                float2 yj = reinterpret_cast<const float2*>(Y)[j];
-                float d0 = yi0 - yj.x, d1 = yi1 - yj.y;
+                const float2 yj = reinterpret_cast<const float2*>(Y)[j];
+                const double d0 = (double)yi0 - (double)yj.x, d1 = (double)yi1 - (double)yj.y;
                 d2 = d0 * d0 + d1 * d1;
             } else {
-                float d0 = yi0 - Y[j];
+                const double d0 = (double)yi0 - (double)Y[j];
                 d2 = d0 * d0;
             }
-            acc += (double)p * ((double)logf(p) + (double)log1pf(d2));
+            acc += (double)p * (log((double)p) + log1p(d2));
             psum += (double)p;
         }
     }

@@ -37,7 +37,10 @@ int fail(int code, const char* msg, cudaError_t e = cudaSuccess) {
 }
 
 // Once per device, with that device current: the device address of the
-// scratch array (in host code its name is only a host-side stand-in).
+// scratch array (in host code its name is only a host-side stand-in). The
+// address is kept for the life of the process: after cudaDeviceReset the
+// module may be loaded again at another address, so this entry point must not
+// be called on a device that the process has reset.
 int setup(int dev, void** ptr, int* sms) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {

@@ -270,6 +270,40 @@ def test_interval_cap_and_fixed_count():
         assert rel_l2(dY.cpu().numpy(), ref["dY"]) <= DY_TOL
 
 
+@pytest.mark.parametrize("scale,fixed,n_int_want", [(140.0, 0, None), (900.0, 0, 1000), (15.0, 1000, 1000)])
+def test_1d_large_grid(scale, fixed, n_int_want):
+    """Workload 3's 1-D grid (Algorithm 1, Sec. 2.5): the interval rule at a
+    width of several hundred, the rule capped at 1000 intervals, and a fixed
+    count of 1000 on a narrow embedding: 3000 nodes and an FFT length of at
+    least 6000 convolved in one CTA. dY, its repulsive part and Z against the
+    oracle at the same tolerances as the small grids; N_int, y_min and b bit
+    for bit."""
+    N = 5003
+    P = affinities(N, 17)
+    Y = clustered_Y(N, 1, scale, seed=int(scale) + fixed, n_clusters=9)
+    with pkg.Plan(N, 1, n_intervals=fixed) as plan:
+        Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+        Yd = torch.as_tensor(Y, device="cuda")
+        dY, Z = plan.gradient(Pd, Yd, alpha=4.0)
+        rep, _ = plan.gradient(Pd, Yd, alpha=0.0)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        info = plan.info()
+    ref = oracle.interp_gradient(Y.astype(np.float64), P.as_tuple(), alpha=4.0, opts=oracle_opts(1, fixed))
+    bx = ref["box"]
+    assert info["n_int"] == bx.n_int
+    if n_int_want is not None:
+        assert bx.n_int == n_int_want
+        assert info["fft_len"] >= 6000
+    else:
+        assert 300 < bx.n_int < 1000
+    assert np.float32(info["y_min"]) == np.float32(bx.y_min)
+    assert np.float32(info["b"]) == np.float32(bx.b)
+    assert rel_l2(dY.cpu().numpy(), ref["dY"]) <= DY_TOL
+    assert rel_l2(rep.cpu().numpy(), 4.0 * ref["rep"]) <= DY_TOL
+    assert abs(Z.item() - ref["Z"]) <= Z_TOL * ref["Z"]
+
+
 def test_errors_are_reported():
     with pytest.raises(pkg.TsneError) as e:
         pkg.Plan(100, 3)
@@ -341,7 +375,7 @@ def test_locality_relabelling(s):
     Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
     out = {}
     for tag, first in (("plain", -1), ("relabel", 5), ("relabel2", 5)):
-        with pkg.Plan(N, s, relabel_first=first, relabel_every=10) as plan:
+        with pkg.Plan(N, s, relabel_first=first, relabel_every=10, order_rounds=-1) as plan:
             Y = torch.as_tensor(Y0.copy(), device="cuda")
             kl = plan.run(Pd, Y, sched)
             assert plan.status() == 0
@@ -349,6 +383,82 @@ def test_locality_relabelling(s):
     assert np.array_equal(out["relabel"][1], out["relabel2"][1])
     assert np.array_equal(out["relabel"][1], out["plain"][1])
     assert out["relabel"][0] == out["plain"][0]
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_graph_order_is_bitwise_neutral(s):
+    """Runs that start in the graph order of P (computed at the run's start,
+    kept for the next run of the same P, or prepared by tsne_plan_order and
+    reused without copying P again; with and without later embedding
+    relabellings; 1 and 8 averaging rounds) equal the run in the caller's
+    labels bit for bit, Y and KL. Rows of very different lengths and an
+    empty row are included."""
+    N = 6000
+    P = affinities(N, 14)
+    # an empty row: drop row 17's entries (P need not be symmetric here)
+    a, b = int(P.row_ptr[17]), int(P.row_ptr[18])
+    col = np.delete(P.col, np.s_[a:b])
+    val = np.delete(P.val, np.s_[a:b])
+    rp = P.row_ptr.copy()
+    rp[18:] -= b - a
+    Pd = pkg.DeviceCSR.from_host(rp, col, val)
+    Y0 = clustered_Y(N, s, 3.0, seed=35)
+    sched = pkg.Schedule(n_iter=30)
+
+    def run(plan):
+        Y = torch.as_tensor(Y0.copy(), device="cuda")
+        kl = plan.run(Pd, Y, sched)
+        assert plan.status() == 0
+        return kl, Y.cpu().numpy()
+
+    with pkg.Plan(N, s, relabel_first=-1, order_rounds=-1) as plan:
+        want = run(plan)
+    cases = []
+    for rounds in (1, 8):
+        for first in (-1, 5):
+            with pkg.Plan(N, s, relabel_first=first, relabel_every=10, order_rounds=rounds) as plan:
+                cases.append(run(plan))          # order computed at the start
+                cases.append(run(plan))          # order kept, copy of P rebuilt
+                plan.order(Pd)                   # prepared: copy of P reused
+                cases.append(run(plan))
+                cases.append(run(plan))
+    for kl, Y in cases:
+        assert np.array_equal(Y, want[1])
+        assert kl == want[0]
+
+
+def test_plan_order_during_a_run():
+    """tsne_plan_order between two pieces of a relabelled run (its copy of P
+    replaced by the graph-ordered one) leaves the run's result bitwise equal
+    to the uninterrupted run."""
+    N = 3000
+    P = affinities(N, 16)
+    Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+    Y0 = inputs.initial_embedding(N, 2, seed=3)
+    sched = pkg.Schedule(n_iter=20)
+    with pkg.Plan(N, 2, relabel_first=2, relabel_every=6) as plan:
+        Ya = torch.as_tensor(Y0.copy(), device="cuda")
+        plan.run_reset()
+        plan.run_iters(Pd, Ya, sched, 0, 20)
+        Yb = torch.as_tensor(Y0.copy(), device="cuda")
+        plan.run_reset()
+        plan.run_iters(Pd, Yb, sched, 0, 5)
+        plan.order(Pd)
+        plan.run_iters(Pd, Yb, sched, 5, 15)
+        assert plan.status() == 0
+    assert torch.equal(Ya, Yb)
+
+
+def test_plan_order_rejections():
+    N = 500
+    P = affinities(N, 15)
+    Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+    with pkg.Plan(N, 2, order_rounds=-1) as plan:
+        with pytest.raises(pkg.TsneError):
+            plan.order(Pd)  # the plan has no graph order
+    with pkg.Plan(N, 2) as plan:
+        with pytest.raises(ValueError):
+            plan.order(pkg.DeviceCSR.from_host(*affinities(N + 1, 15).as_tuple()))
 
 
 @pytest.mark.parametrize("s", [1, 2])

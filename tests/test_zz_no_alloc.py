@@ -49,3 +49,18 @@ def test_kl_noalloc_rejects_bad_sizes():
         pkg.tsne_kl_noalloc(Pd, Y, 3, 1.0, out)
     with pytest.raises(pkg.TsneError):
         pkg.tsne_kl_noalloc(Pd, Y, 2, 0.0, out)
+
+
+def test_kl_noalloc_rejects_mismatched_y():
+    """Y must hold P's N points as contiguous float32 on the device: a Y with
+    fewer rows than P (the kernel would read past its end), a float64 Y and a
+    host Y are rejected before the call."""
+    Pd = pkg.DeviceCSR.from_host(np.array([0, 1, 2, 2], np.int32), np.array([1, 0], np.int32),
+                                 np.array([0.5, 0.5], np.float32))
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        pkg.tsne_kl_noalloc(Pd, torch.zeros((2, 2), device="cuda"), 2, 1.0, out)
+    with pytest.raises(TypeError):
+        pkg.tsne_kl_noalloc(Pd, torch.zeros((3, 2), dtype=torch.float64, device="cuda"), 2, 1.0, out)
+    with pytest.raises(TypeError):
+        pkg.tsne_kl_noalloc(Pd, torch.zeros((3, 2)), 2, 1.0, out)
