@@ -9,7 +9,8 @@ produced.
 The arithmetic lives in ``fitsne_oracle.c`` (built here with gcc,
 ``-O2 -ffp-contract=off -fopenmp``); this module only marshals numpy arrays.
 ``affinities.py`` holds the oracle's own input-affinity builder (Sec. 1.1,
-Eq. p_ij); ``heatmap.py`` the t-SNE heatmaps of Sec. 5.
+Eq. p_ij); ``heatmap.py`` the t-SNE heatmaps of Sec. 5; ``oocpca.py`` the
+out-of-core randomized PCA of Sec. 6 (Algorithm oocPCA).
 
 Parity status of each function (what pins it is in tests/test_oracle_*.py):
   exact_gradient      pinned: finite differences of KL, closed forms, invariants
@@ -22,6 +23,9 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   heatmap.bins        pinned: hand-worked bins, the FP32 decision at a bin edge
   heatmap.gene_bin_sums  pinned: one-hot sparse product, column totals
   heatmap.nearest     pinned: scipy cdist, a planted tie, brute force
+  oocpca.oocpca       pinned: planted rank and spectrum, dense SVD (LAPACK),
+                      blocking invariance, centring, power-iteration gain
+  oocpca.lu_renormalize  pinned: L U = Y, |L| <= 1, permuted unit trapezoid
 """
 from __future__ import annotations
 

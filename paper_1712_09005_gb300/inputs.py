@@ -268,3 +268,53 @@ def expression(N: int, G: int, mean_genes: float = 1000.0, n_clusters: int = 20,
     np.cumsum(np.bincount(cell, minlength=N), out=row_ptr[1:])
     return Expression(y, row_ptr.astype(np.int32), (uk % G).astype(np.int32), cnt.astype(np.float32), G,
                       label)
+
+
+# ---- out-of-core PCA inputs (Sec. 6) -------------------------------------------
+
+def planted_spectrum(rank: int, top: float = 100.0, ratio: float = 1e-2) -> np.ndarray:
+    """Singular values decaying geometrically from top to top * ratio."""
+    if rank == 1:
+        return np.array([top])
+    return top * ratio ** (np.arange(rank) / (rank - 1))
+
+
+def low_rank_matrix(m: int, n: int, rank: int, seed: int, sigma=None, noise: float = 0.0,
+                    device: str = "cpu", dtype=None):
+    """A = U0 diag(sigma) V0* (+ noise * N(0, 1) entries) with U0, V0
+    orthonormal (QR of Gaussian matrices), the shape of the paper's random
+    rank-50 test matrix. Returns (A, sigma, U0, V0): numpy FP64 on the CPU;
+    on a CUDA device, torch tensors (A in dtype, default float32) built with
+    torch on that device (the paper's 1,000,000 x 30,000 size needs 120 GB
+    in FP32, so it is generated where it is used)."""
+    sigma = planted_spectrum(rank) if sigma is None else np.asarray(sigma, np.float64)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if device == "cpu":
+        U0, _ = np.linalg.qr(rng.standard_normal((m, rank)))
+        V0, _ = np.linalg.qr(rng.standard_normal((n, rank)))
+        A = (U0 * sigma) @ V0.T
+        if noise:
+            A += noise * rng.standard_normal((m, n))
+        if dtype is not None:
+            A = A.astype(dtype)
+        return A, sigma, U0, V0
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    U0, _ = torch.linalg.qr(torch.randn(m, rank, generator=g, device=device, dtype=torch.float64))
+    V0, _ = torch.linalg.qr(torch.randn(n, rank, generator=g, device=device, dtype=torch.float64))
+    s = torch.as_tensor(sigma, device=device)
+    dt = dtype or torch.float32
+    A = torch.empty((m, n), device=device, dtype=dt)
+    step = max(1, (1 << 28) // max(1, n))  # rows per slab of the product (FP64 slab <= 2 GB)
+    for r0 in range(0, m, step):
+        slab = (U0[r0:r0 + step] * s) @ V0.T
+        if noise:
+            slab += noise * torch.randn(slab.shape, generator=g, device=device, dtype=torch.float64)
+        A[r0:r0 + step] = slab.to(dt)
+    return A, sigma, U0, V0
+
+
+def omega(n: int, l: int, seed: int) -> np.ndarray:
+    """Omega of Algorithm oocPCA: n x l uniform on [-1, 1) (FP64)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 104729))
+    return rng.uniform(-1.0, 1.0, size=(n, l))
