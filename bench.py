@@ -481,11 +481,11 @@ def run_ours(a):
         plan.run_iters(Pd, Yw, sched, 0, W)
     torch.cuda.synchronize()
 
-    # timed: iterations 0 .. K-1 of the job from Y0
+    # timed: iterations 0 .. K-1 of the job from Y0 (steady-state steps
+    # replay the plan's step graph; no per-phase events in this pass)
     Y = torch.as_tensor(Y0.copy(), device="cuda")
     plan.run_reset()
-    plan.profile(True)
-    plan.profile_read()
+    plan.profile(False)
     launches0 = plan.launch_count()
     clocks = ClockSampler(local)
     if world > 1:
@@ -504,12 +504,21 @@ def run_ours(a):
     clk = clocks.stop()
     launches = plan.launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
-    prof = plan.profile_read()
-    plan.profile(False)
     info = plan.info()
     status = plan.status()
     if status != 0:
         raise RuntimeError(f"device status {status} after the timed run")
+    # the same K iterations again with CUDA events around every phase on the
+    # plan's stream (plain launches): the per-phase times and the force
+    # kernel's duration for the roofline
+    Yp = torch.as_tensor(Y0.copy(), device="cuda")
+    plan.run_reset()
+    plan.profile(True)
+    plan.profile_read()
+    plan.run_iters(Pd, Yp, sched, 0, K)
+    prof = plan.profile_read()
+    plan.profile(False)
+    del Yp
     ms_max = max_over_ranks(ms)
     value = whole_job_rate(world, N, K, ms_max / 1e3)
 
@@ -534,8 +543,6 @@ def run_ours(a):
     if K < n_iter and not a.no_full_job:
         Yf = torch.as_tensor(Y0.copy(), device="cuda")
         plan.run_reset()
-        plan.profile(True)
-        plan.profile_read()
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -544,17 +551,23 @@ def run_ours(a):
         f1.record(stream)
         torch.cuda.synchronize()
         fms = f0.elapsed_time(f1)
-        fprof = plan.profile_read()
-        plan.profile(False)
         finfo = plan.info()
         if plan.status() != 0:
             raise RuntimeError("device status after the full job")
+        Yf = torch.as_tensor(Y0.copy(), device="cuda")  # phases of the whole job (events, plain launches)
+        plan.run_reset()
+        plan.profile(True)
+        plan.profile_read()
+        plan.run_iters(Pd, Yf, sched, 0, n_iter)
+        fprof = plan.profile_read()
+        plan.profile(False)
         full_job = {"iterations": [0, n_iter], "value": N * n_iter / (fms / 1e3), "unit": UNIT,
                     "ms_per_step": fms / n_iter,
                     "phases_ms_per_iter": {k: v / max(1, fprof["evals"]) for k, v in fprof["ms"].items()},
                     "final_n_int": finfo["n_int"], "final_fft_len": finfo["fft_len"],
                     "note": "the same job from Y0 over its whole schedule, CUDA events on the plan's "
-                            "stream; starts in the order prepared before the timed region"}
+                            "stream around the run; starts in the order prepared before the timed "
+                            "region; phases from a second run with per-phase events"}
         del Yf
 
     # end to end through the C ABI with host buffers (pinned): upload P and
@@ -613,6 +626,9 @@ def run_ours(a):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "force_kernel (attraction + interpolation + update)",
+                         "duration": "mean CUDA-event time of the force phase over a second pass of "
+                                     "the same K iterations with per-phase events (the timed pass "
+                                     "replays a graph)",
                          "algorithmic_bytes_per_launch": bytes_force,
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "iteration_roofline": {"bound": "hbm", "achieved": iter_achieved, "peak": peak,

@@ -32,7 +32,9 @@ __all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destr
            "tsne_affinity_destroy", "tsne_affinity_compute", "tsne_affinity_knn_copy",
            "tsne_affinity_phase_ms", "tsne_affinity_launch_count", "Heatmap", "tsne_heatmap_create",
            "tsne_heatmap_destroy", "tsne_heatmap_bin", "tsne_heatmap_nearest", "tsne_heatmap_phase_ms",
-           "tsne_heatmap_launch_count"]
+           "tsne_heatmap_launch_count", "OocPca", "tsne_oocpca_create", "tsne_oocpca_destroy",
+           "tsne_oocpca_run", "tsne_oocpca_debug_copy", "tsne_oocpca_phase_ms",
+           "tsne_oocpca_launch_count"]
 
 
 def lib():
@@ -747,3 +749,106 @@ class Plan:
 
     def launch_count(self) -> int:
         return tsne_plan_launch_count(self.handle)
+
+
+# ---- out-of-core randomized PCA (Sec. 6, Algorithm oocPCA) ---------------------
+
+def tsne_oocpca_create(m: int, n: int, k: int, l: int, its: int = 0, center: bool = False,
+                       block_rows: int = 0, stream: int | None = None) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    opts = _abi.tsne_oocpca_opts(its, 1 if center else 0, block_rows, stream)
+    out = ctypes.c_void_p()
+    check(lib().tsne_oocpca_create(m, n, k, l, ctypes.byref(opts), ctypes.byref(out)))
+    return out
+
+
+def tsne_oocpca_destroy(plan) -> None:
+    check(lib().tsne_oocpca_destroy(plan))
+
+
+def tsne_oocpca_run(plan, A_ptr: int, lda: int, a_on_host: bool, Omega: torch.Tensor, U: torch.Tensor,
+                    sigma: torch.Tensor, V: torch.Tensor) -> None:
+    check(lib().tsne_oocpca_run(plan, ctypes.c_void_p(A_ptr), lda, 1 if a_on_host else 0, _ptr(Omega),
+                                _ptr(U), _ptr(sigma), _ptr(V)))
+
+
+def tsne_oocpca_debug_copy(plan, which: int, rows: int, l: int) -> np.ndarray:
+    out = np.empty((rows, l), np.float64)
+    check(lib().tsne_oocpca_debug_copy(plan, which, out.ctypes.data_as(ctypes.c_void_p), out.nbytes))
+    return out
+
+
+def tsne_oocpca_phase_ms(plan) -> tuple[list[float], int]:
+    ms = (ctypes.c_double * 4)()
+    passes = ctypes.c_int32()
+    check(lib().tsne_oocpca_phase_ms(plan, ms, ctypes.byref(passes)))
+    return list(ms), passes.value
+
+
+def tsne_oocpca_launch_count(plan) -> int:
+    return int(lib().tsne_oocpca_launch_count(plan))
+
+
+class OocPca:
+    """Owns a tsne_oocpca plan: top-k PCA of an m x n FP32 matrix held on the
+    device (a torch tensor) or in host memory (a numpy array, pinned or not),
+    read block by block."""
+
+    def __init__(self, m: int, n: int, k: int, l: int | None = None, its: int = 0,
+                 center: bool = False, block_rows: int = 0, stream: int | None = None):
+        self.m, self.n, self.k = m, n, k
+        self.l = k + 2 if l is None else l
+        self.handle = tsne_oocpca_create(m, n, k, self.l, its, center, block_rows, stream)
+
+    def run(self, A, Omega):
+        """A: torch CUDA float32 (m x n, row stride a multiple of 4) or a host
+        float32 array; Omega: n x l. Returns (U, sigma, V) as CUDA tensors."""
+        if isinstance(A, torch.Tensor) and A.is_cuda:
+            if A.dtype != torch.float32 or A.dim() != 2 or A.stride(1) != 1 or tuple(A.shape) != (self.m, self.n):
+                raise TypeError("A must be a CUDA float32 m x n tensor with unit column stride")
+            ptr, lda, host = A.data_ptr(), A.stride(0), False
+        else:
+            if isinstance(A, torch.Tensor):
+                A = A.numpy()
+            if A.dtype != np.float32 or A.ndim != 2 or A.shape != (self.m, self.n) or A.strides[1] != 4:
+                raise TypeError("A must be a float32 m x n array with unit column stride")
+            ptr, lda, host = A.ctypes.data, A.strides[0] // 4, True
+        Om = torch.as_tensor(np.asarray(Omega, np.float32) if not isinstance(Omega, torch.Tensor) else Omega,
+                             device="cuda", dtype=torch.float32).contiguous()
+        if tuple(Om.shape) != (self.n, self.l):
+            raise ValueError(f"Omega must be {self.n} x {self.l}")
+        U = torch.empty((self.m, self.k), device="cuda", dtype=torch.float32)
+        V = torch.empty((self.n, self.k), device="cuda", dtype=torch.float32)
+        sig = torch.empty(self.k, device="cuda", dtype=torch.float64)
+        tsne_oocpca_run(self.handle, ptr, lda, host, Om, U, sig, V)
+        return U, sig, V
+
+    def debug(self, which: int) -> np.ndarray:
+        rows = self.n if which == 1 else self.m
+        return tsne_oocpca_debug_copy(self.handle, which, rows, self.l)
+
+    def phase_ms(self):
+        ms, passes = tsne_oocpca_phase_ms(self.handle)
+        return {"passes_ms": ms[0], "renormalize_ms": ms[1], "qr_svd_ms": ms[2], "means_ms": ms[3],
+                "passes": passes}
+
+    def launch_count(self) -> int:
+        return tsne_oocpca_launch_count(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            tsne_oocpca_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -78,7 +78,13 @@ class tsne_batch_tuning(ctypes.Structure):
                 ("n_int_policy", ctypes.c_int32), ("ms_per_iter", ctypes.c_float)]
 
 
+class tsne_oocpca_opts(ctypes.Structure):
+    _fields_ = [("its", ctypes.c_int32), ("center", ctypes.c_int32), ("block_rows", ctypes.c_int64),
+                ("stream", ctypes.c_void_p)]
+
+
 # (name, restype, argtypes) for every entry point of include/fitsne_gb300.h
+# and include/oocpca_gb300.h
 _P = ctypes.c_void_p
 _SIGNATURES = [
     ("tsne_version", ctypes.c_char_p, []),
@@ -152,6 +158,14 @@ _SIGNATURES = [
     ("tsne_heatmap_nearest", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     ("tsne_heatmap_phase_ms", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("tsne_heatmap_launch_count", ctypes.c_int64, [_P]),
+    ("tsne_oocpca_create", ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(tsne_oocpca_opts), ctypes.POINTER(_P)]),
+    ("tsne_oocpca_destroy", ctypes.c_int, [_P]),
+    ("tsne_oocpca_run", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P]),
+    ("tsne_oocpca_debug_copy", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t]),
+    ("tsne_oocpca_phase_ms", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    ("tsne_oocpca_launch_count", ctypes.c_int64, [_P]),
 ]
 
 _lock = threading.Lock()

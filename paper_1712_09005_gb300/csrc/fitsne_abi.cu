@@ -301,6 +301,10 @@ void free_prof(tsne_plan* pl) {
 
 void free_plan(tsne_plan* pl) {
     free_prof(pl);
+    if (pl->step_exec) cudaGraphExecDestroy(pl->step_exec);
+    if (pl->g_in) cudaEventDestroy(pl->g_in);
+    if (pl->g_out) cudaEventDestroy(pl->g_out);
+    if (pl->gstream) cudaStreamDestroy(pl->gstream);
     fitsne::fft_set_destroy(&pl->fft);
     void* ptrs[] = {pl->job_mem,   pl->d_job,      pl->d_dyn,     pl->kl_partial, pl->kl_ticket,
                     pl->kl_out_dev, pl->valid_flag, pl->y_next,    pl->uY_run,     pl->gains_run,
@@ -367,9 +371,10 @@ void set_csr(tsne_plan* pl, const tsne_csr& P) {
 // The repulsive half of an iteration: box, sort, spread, convolution, Z.
 // With timed set and tracing on, phase events 0..3 are recorded around it;
 // the caller records event 4 after the force kernel.
-int enqueue_field(tsne_plan* pl, bool timed) {
+int enqueue_field(tsne_plan* pl, bool timed, bool advance_first = false) {
     if (timed) prof_begin(pl);
-    CU(fitsne::launch_box(pl->d_job, pl->caps, pl->tables, 0, pl->stream), "box kernel launch");
+    CU(fitsne::launch_box(pl->d_job, pl->caps, pl->tables, 0, pl->stream, advance_first ? 1 : 0),
+       "box kernel launch");
     pl->launches += 1;
     if (timed) prof_mark(pl, 1);
     CU(fitsne::launch_sort_and_spread(pl->d_job, pl->caps, pl->stream), "sort/spread launch");
@@ -721,6 +726,47 @@ static int relabel(tsne_plan* plan, const tsne_csr& P, float* cur, float* nxt) {
     return TSNE_OK;
 }
 
+// Captures the steady-state step (a step whose predecessor's advance is
+// still pending) on the plan's private stream. The kernels read the job
+// table in device memory, so one graph serves every such step of every run
+// of the plan (relabellings rewrite the table, not the launches).
+static int build_step_graph(tsne_plan* plan) {
+    if (!plan->gstream) {
+        CU(cudaStreamCreateWithFlags(&plan->gstream, cudaStreamNonBlocking), "graph stream");
+        CU(cudaEventCreateWithFlags(&plan->g_in, cudaEventDisableTiming), "graph event");
+        CU(cudaEventCreateWithFlags(&plan->g_out, cudaEventDisableTiming), "graph event");
+    }
+    cudaStream_t user = plan->stream;
+    const int prof = plan->profiling;
+    const int64_t l0 = plan->launches;
+    plan->stream = plan->gstream;
+    plan->profiling = 0;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(plan->gstream, cudaStreamCaptureModeThreadLocal);
+    int rc = TSNE_OK;
+    if (e == cudaSuccess) {
+        rc = enqueue_field(plan, false, true);
+        if (rc == TSNE_OK) rc = enqueue_forces(plan, 1);
+        e = cudaStreamEndCapture(plan->gstream, &g);
+    }
+    plan->stream = user;
+    plan->profiling = prof;
+    plan->step_kernels = (int)(plan->launches - l0);
+    plan->launches = l0;
+    if (rc != TSNE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "step capture");
+    e = cudaGraphInstantiate(&plan->step_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        plan->step_exec = nullptr;
+        return cuda_fail(e, "step graph instantiation");
+    }
+    return TSNE_OK;
+}
+
 // Iterations it0 .. it0+count-1. The table row holds ybuf = {y_cur, y_next};
 // the device flips the current buffer after every step (advance kernel), the
 // host follows the parity. Y (in the caller's labels) holds the input and
@@ -754,22 +800,63 @@ static int run_iters(tsne_plan* plan, const tsne_csr& P, float* Y, const tsne_st
     const JobDyn d{it0, 0, 0, 0};
     if (int rc = upload_job(plan, &d)) return rc;
     int par = 0;
+    // the move of the job to its next iteration after a step is left to the
+    // next step's bounding-box kernel (or to an advance launch before a
+    // relabelling and at the end of the call)
+    bool pending = false;
+    // steady-state steps replay the step graph on gstream (one host call per
+    // step) unless the phases are being traced
+    const bool use_graph = !plan->profiling;
+    bool in_graph = false;  // gstream holds the latest work
+    auto join = [&]() -> int {
+        if (!in_graph) return TSNE_OK;
+        CU(cudaEventRecord(plan->g_out, plan->gstream), "graph fence");
+        CU(cudaStreamWaitEvent(plan->stream, plan->g_out, 0), "graph fence");
+        in_graph = false;
+        return TSNE_OK;
+    };
+    auto advance = [&]() -> int {
+        if (int rc = join()) return rc;
+        CU(fitsne::launch_advance(plan->d_job, 1, plan->stream), "advance launch");
+        plan->launches += 1;
+        pending = false;
+        return TSNE_OK;
+    };
     for (int it = it0; it < it0 + count; ++it) {
         if (it == 0 && !plan->reordered && plan->order_rounds > 0) {
+            if (pending)
+                if (int rc = advance()) return rc;
             if (int rc = graph_relabel(plan, P, buf[par], buf[par ^ 1])) return rc;
             set_p();
             if (int rc = upload_job(plan, nullptr)) return rc;
         } else if (relabel_at(plan, it)) {
+            if (pending)
+                if (int rc = advance()) return rc;
             if (int rc = relabel(plan, P, buf[par], buf[par ^ 1])) return rc;
             set_p();
             if (int rc = upload_job(plan, nullptr)) return rc;
         }
-        if (int rc = enqueue_field(plan, true)) return rc;
-        if (int rc = enqueue_forces(plan, 1)) return rc;
-        CU(fitsne::launch_advance(plan->d_job, 1, plan->stream), "advance launch");
-        plan->launches += 1;
+        if (use_graph && pending) {
+            if (!plan->step_exec)
+                if (int rc = build_step_graph(plan)) return rc;
+            if (!in_graph) {
+                CU(cudaEventRecord(plan->g_in, plan->stream), "graph fence");
+                CU(cudaStreamWaitEvent(plan->gstream, plan->g_in, 0), "graph fence");
+                in_graph = true;
+            }
+            CU(cudaGraphLaunch(plan->step_exec, plan->gstream), "step graph launch");
+            plan->launches += plan->step_kernels;
+        } else {
+            if (int rc = join()) return rc;
+            if (int rc = enqueue_field(plan, true, pending)) return rc;
+            if (int rc = enqueue_forces(plan, 1)) return rc;
+        }
+        pending = true;
         par ^= 1;
     }
+    if (int rc = join()) return rc;
+    if (pending)
+        if (int rc = advance()) return rc;
     if (plan->reordered) CU(fitsne::launch_to_labels(plan, buf[par], 1, Y), "Y to caller labels");
     else CU(cudaMemcpyAsync(Y, buf[par], sizeof(float) * ns, cudaMemcpyDeviceToDevice, plan->stream), "Y copy");
     return TSNE_OK;

@@ -22,7 +22,7 @@ constexpr int kWarp = 32;
 constexpr int kMaxStages = 16;    // radix stages of one FFT
 constexpr int kScanBlock = 2048;  // boxes per scan work item (1024 threads x 2)
 constexpr int kBoxThreads = 256;  // threads of the bounding-box blocks
-constexpr int kBoxBlocks = 304;   // bounding-box work items of a large job (2 per SM)
+constexpr int kBoxBlocks = 608;   // bounding-box work items of a large job (4 per SM)
 constexpr int kHistBins = 11776;  // boxes of a shared-memory histogram (46 KB: with the
                                   // job split it stays under the 48 KB default limit)
 constexpr int kSortPts = 2048;    // points per work item of the sort kernels (256 threads x 8)
@@ -258,6 +258,12 @@ struct tsne_plan {
     int p2_is_run;           // rp2/col2/val2 hold the run's P in the run's order (perm/inv)
     float* order_z;          // [4 N] two float2 coordinate buffers
     double* order_stats;     // [4 * 256 + 2] block partials, then the key window (4 floats)
+    // steady-state step of a run as a CUDA graph (box with the deferred
+    // advance, sort, spread, FFT, forces), replayed on gstream; built on first use
+    cudaStream_t gstream;
+    cudaGraphExec_t step_exec;
+    int step_kernels;        // kernels of one replay
+    cudaEvent_t g_in, g_out; // fences between the plan's stream and gstream
     // force kernel scheduling
     int force_mode;          // TSNE_FORCE_* (plan option)
     int n_regions;           // SM id range of the device
@@ -394,9 +400,11 @@ __device__ __forceinline__ void lagrange(float t, float (&Lw)[PP]) {
 // caps give per-table upper bounds of the work (see TableCaps).
 // ----------------------------------------------------------------------------
 
-// ignore_schedule: every job is active with alpha from the job (KL passes)
+// ignore_schedule: every job is active with alpha from the job (KL passes);
+// advance_first: stepping jobs first move to their next iteration (what
+// launch_advance does), so that no advance kernel runs between two steps
 cudaError_t launch_box(const Job* jobs, const TableCaps& c, const Tables& t, int ignore_schedule,
-                       cudaStream_t st);
+                       cudaStream_t st, int advance_first = 0);
 cudaError_t launch_sort_and_spread(const Job* jobs, const TableCaps& c, cudaStream_t st);
 cudaError_t launch_convolution(const Job* jobs, const TableCaps& c, const Tables& t,
                                cudaStream_t st);

@@ -92,6 +92,73 @@ __device__ __forceinline__ int scan_items(const Job& J) {
 
 }  // namespace
 
+// The box, interval count, node spacing, FFT length and schedule values of
+// a job's iteration `it` (Y in ybuf[cur]) from the exact min / max of its
+// coordinates (Sec. 2.2, 2.4, 2.5; Sec. 1.2 and Sec. 4 exaggeration). The
+// FP32 rule matches the oracle's bit for bit. One thread.
+__device__ void box_finish(const Job& J, int s, int p, const Tables& tab, int ignore_schedule,
+                           float lo, float hi, bool any_bad, int cur, int it) {
+    Params P;
+    P.error = __ldcg(&J.params->error);
+    if (any_bad) { P.error = TSNE_ERR_NONFINITE; lo = 0.0f; hi = 1.0f; }
+    float y_min, width;
+    int n_int;
+    if (J.force_box) {
+        y_min = J.force_y_min;
+        width = J.force_width;
+        n_int = J.force_n_int;
+    } else {
+        y_min = lo;
+        width = __fsub_rn(hi, lo);
+        if (!(width > 0.0f)) width = 1.0f;
+        if (J.n_int_fixed > 0) {
+            n_int = J.n_int_fixed;
+        } else {
+            float c = ceilf(width);
+            if (c > (float)J.n_int_max) c = (float)J.n_int_max;
+            n_int = (int)c;
+            if (n_int < J.n_min) n_int = J.n_min;
+            if (n_int > J.n_int_max) n_int = J.n_int_max;
+            if (J.n_int_table) n_int = J.n_int_table[n_int];
+        }
+    }
+    P.y_min = y_min;
+    P.width = width;
+    P.n_int = n_int;
+    P.b = __fdiv_rn(width, (float)n_int);
+    P.inv_b = __fdiv_rn(1.0f, P.b);
+    P.delta = __fdiv_rn(P.b, (float)p);
+    P.inv_delta = __fdiv_rn((float)p, P.b);
+    P.delta2 = __fmul_rn(P.delta, P.delta);
+    P.fx_shift = J.fx_shift;
+    P.fx_scale = ldexpf(1.0f, J.fx_shift);
+    P.fx_inv = ldexpf(1.0f, -J.fx_shift);
+    P.n = p * n_int;
+    P.n_boxes = (s == 2) ? n_int * n_int : n_int;
+    const int idx = tab.fft_of_n[P.n];
+    P.fft_idx = idx;
+    P.L = tab.fft[idx].L;
+    P.p_f = (float)p;
+    P.n_chunks = 0;
+    P.Z = 0.0;
+    P.inv_Z = 0.0f;
+    P.active = 1;
+    P.cur = cur;
+    P.pad = 0;
+    if (J.mode == kModeStep && !ignore_schedule) {
+        float a = 1.0f;
+        if (it < J.early_iters) a = J.early_alpha;
+        else if (J.late_iters > 0 && it >= J.n_iter - J.late_iters) a = J.late_alpha;
+        P.alpha = a;
+        P.momentum = it < J.mom_switch_iter ? J.momentum_early : J.momentum_late;
+    } else {
+        P.alpha = J.alpha;
+        P.momentum = 0.0f;
+    }
+    *J.params = P;
+    J.dyn->error = P.error;
+}
+
 // ----------------------------------------------------------------------------
 // Bounding box: per-item min/max, then the last item of a job to finish
 // derives the box, N_int, node spacing, FFT length and the iteration's
@@ -100,7 +167,7 @@ __device__ __forceinline__ int scan_items(const Job& J) {
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBoxThreads)
 box_kernel(const Job* __restrict__ jobs, int njobs, int s, int p, int ignore_schedule,
-           Tables tab) {
+           Tables tab, int advance_first) {
     __shared__ int32_t s_start[kMaxJobs + 1];
     __shared__ float s_lo[kBoxThreads / 32], s_hi[kBoxThreads / 32];
     __shared__ bool s_last;
@@ -115,7 +182,12 @@ box_kernel(const Job* __restrict__ jobs, int njobs, int s, int p, int ignore_sch
             if (threadIdx.x == 0) J.params->active = 0;
             continue;  // uniform over the block
         }
-        const int cur = J.dyn->cur;
+        // advance_first: the previous step's move to the next iteration (new Y
+        // current, schedule index + 1) happens here instead of in a kernel of
+        // its own; every item reads the advanced values, the last one stores them
+        const int adv = (advance_first && J.mode == kModeStep) ? 1 : 0;
+        const int cur = J.dyn->cur ^ adv;
+        const int it_now = J.dyn->iter + adv;
         const float* __restrict__ Y = J.ybuf[cur];
         const int64_t count = J.N * s;
         float lo = INFINITY, hi = -INFINITY;
@@ -125,6 +197,7 @@ box_kernel(const Job* __restrict__ jobs, int njobs, int s, int p, int ignore_sch
         if ((reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
             const int64_t n4 = count / 4;
             const float4* Y4 = reinterpret_cast<const float4*>(Y);
+#pragma unroll 4
             for (int64_t q = k0; q < n4; q += stride) {
                 float4 v = __ldg(&Y4[q]);
                 bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
@@ -184,66 +257,11 @@ box_kernel(const Job* __restrict__ jobs, int njobs, int s, int p, int ignore_sch
             if (threadIdx.x == 0) {
                 for (int i = 0; i < kBoxThreads / 32; ++i) { lo = fminf(lo, s_lo[i]); hi = fmaxf(hi, s_hi[i]); }
                 J.tickets[0] = 0u;
-                Params P;
-                P.error = __ldcg(&J.params->error);
-                if (any_bad) { P.error = TSNE_ERR_NONFINITE; lo = 0.0f; hi = 1.0f; }
-                float y_min, width;
-                int n_int;
-                if (J.force_box) {
-                    y_min = J.force_y_min;
-                    width = J.force_width;
-                    n_int = J.force_n_int;
-                } else {
-                    y_min = lo;
-                    width = __fsub_rn(hi, lo);
-                    if (!(width > 0.0f)) width = 1.0f;
-                    if (J.n_int_fixed > 0) {
-                        n_int = J.n_int_fixed;
-                    } else {
-                        float c = ceilf(width);
-                        if (c > (float)J.n_int_max) c = (float)J.n_int_max;
-                        n_int = (int)c;
-                        if (n_int < J.n_min) n_int = J.n_min;
-                        if (n_int > J.n_int_max) n_int = J.n_int_max;
-                        if (J.n_int_table) n_int = J.n_int_table[n_int];
-                    }
+                if (adv) {
+                    J.dyn->cur = cur;
+                    J.dyn->iter = it_now;
                 }
-                P.y_min = y_min;
-                P.width = width;
-                P.n_int = n_int;
-                P.b = __fdiv_rn(width, (float)n_int);
-                P.inv_b = __fdiv_rn(1.0f, P.b);
-                P.delta = __fdiv_rn(P.b, (float)p);
-                P.inv_delta = __fdiv_rn((float)p, P.b);
-                P.delta2 = __fmul_rn(P.delta, P.delta);
-                P.fx_shift = J.fx_shift;
-                P.fx_scale = ldexpf(1.0f, J.fx_shift);
-                P.fx_inv = ldexpf(1.0f, -J.fx_shift);
-                P.n = p * n_int;
-                P.n_boxes = (s == 2) ? n_int * n_int : n_int;
-                const int idx = tab.fft_of_n[P.n];
-                P.fft_idx = idx;
-                P.L = tab.fft[idx].L;
-                P.p_f = (float)p;
-                P.n_chunks = 0;
-                P.Z = 0.0;
-                P.inv_Z = 0.0f;
-                P.active = 1;
-                P.cur = cur;
-                P.pad = 0;
-                if (J.mode == kModeStep && !ignore_schedule) {
-                    const int it = J.dyn->iter;
-                    float a = 1.0f;
-                    if (it < J.early_iters) a = J.early_alpha;
-                    else if (J.late_iters > 0 && it >= J.n_iter - J.late_iters) a = J.late_alpha;
-                    P.alpha = a;
-                    P.momentum = it < J.mom_switch_iter ? J.momentum_early : J.momentum_late;
-                } else {
-                    P.alpha = J.alpha;
-                    P.momentum = 0.0f;
-                }
-                *J.params = P;
-                J.dyn->error = P.error;
+                box_finish(J, s, p, tab, ignore_schedule, lo, hi, any_bad, cur, it_now);
             }
         }
         __syncthreads();  // shared state of this item is consumed
@@ -1138,9 +1156,9 @@ static int grid_cap(int64_t items, int per_block, int64_t cap) {
 }
 
 cudaError_t launch_box(const Job* jobs, const TableCaps& c, const Tables& t, int ignore_schedule,
-                       cudaStream_t st) {
+                       cudaStream_t st, int advance_first) {
     const int g = grid_cap(c.sum_box_items, 1, 4LL * c.sm_count);
-    box_kernel<<<g, kBoxThreads, 0, st>>>(jobs, c.njobs, c.s, c.p, ignore_schedule, t);
+    box_kernel<<<g, kBoxThreads, 0, st>>>(jobs, c.njobs, c.s, c.p, ignore_schedule, t, advance_first);
     return cudaGetLastError();
 }
 

@@ -2,19 +2,22 @@
 entry point include/fitsne_gb300.h declares; host-only entry points behave as
 documented (no device work is issued here)."""
 import ctypes
+import glob
 import os
 import re
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "fitsne_gb300.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(tsne_[a-z_0-9]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(tsne_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -128,3 +131,20 @@ def test_null_heatmap_and_run_state_are_rejected(lib):
     assert lib.tsne_heatmap_launch_count(None) == 0
     assert lib.tsne_run_state_save(None, None, None) == _abi.TSNE_ERR_INVALID_ARG
     assert lib.tsne_run_state_load(None, None, None) == _abi.TSNE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("m,n,k,l", [
+    (1, 100, 2, 4),      # m < 2
+    (100, 102, 2, 4),    # n not a multiple of 4
+    (100, 100, 0, 4),    # k < 1
+    (100, 100, 5, 4),    # l < k
+    (100, 100, 2, 65),   # l > 64
+    (40, 100, 2, 40),    # l >= min(m, n)
+])
+def test_oocpca_create_rejects_bad_arguments(lib, m, n, k, l):
+    from paper_1712_09005_gb300 import _abi
+    out = ctypes.c_void_p()
+    opts = _abi.tsne_oocpca_opts()
+    rc = lib.tsne_oocpca_create(m, n, k, l, ctypes.byref(opts), ctypes.byref(out))
+    assert rc == _abi.TSNE_ERR_INVALID_ARG
+    assert not out.value

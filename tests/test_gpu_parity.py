@@ -526,3 +526,29 @@ def test_force_schedules_agree(s):
     assert np.array_equal(out[(modes[0], "Y")], out[(modes[1], "Y")])
     assert np.array_equal(out[(modes[0], "dY")], out[(modes[1], "dY")])
     assert out[modes[0]] == out[modes[1]]
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_step_graph_equals_plain_launches(s):
+    """Steady-state steps of a run replay one captured CUDA graph (on the
+    plan's own stream, fenced to the caller's); with phase tracing on they
+    are plain launches. Both give the same Y bit for bit, with relabellings
+    inside the run and the run split over two calls."""
+    N = 5000
+    P = affinities(N, 18)
+    Pd = pkg.DeviceCSR.from_host(*P.as_tuple())
+    Y0 = clustered_Y(N, s, 3.0, seed=37)
+    sched = pkg.Schedule(n_iter=40)
+    out = []
+    for trace in (False, True):
+        with pkg.Plan(N, s, relabel_first=7, relabel_every=12) as plan:
+            plan.profile(trace)
+            Y = torch.as_tensor(Y0.copy(), device="cuda")
+            plan.run_reset()
+            plan.run_iters(Pd, Y, sched, 0, 17)
+            plan.run_iters(Pd, Y, sched, 17, 23)
+            assert plan.status() == 0
+            out.append(Y.cpu().numpy())
+            if trace:
+                assert plan.profile_read()["evals"] == 40
+    assert np.array_equal(out[0], out[1])
