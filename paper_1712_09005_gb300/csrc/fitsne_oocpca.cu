@@ -26,12 +26,13 @@
 // (converter warps) between the TMA load and the MMAs; for G2 the converter
 // also transposes the tile, so both products read K-major operands.
 //
-// Warp roles of a GEMM CTA (256 threads): warp 0 issues the TMA loads, warp
+// Warp roles of a GEMM CTA (384 threads): warp 0 issues the TMA loads, warp
 // 1 owns the tensor memory and issues the MMAs (one thread), warps 2..7
-// split (and transpose) the A tiles, warps 4..7 also read the accumulator
-// back (tcgen05.ld: warp w reads lanes 32 (w % 4) .. + 31). Stages are
-// handed over with mbarriers; every wait is bounded: a wait that gives up
-// sets the error word, and the kernel finishes without further MMAs.
+// split (and transpose) the A tiles, warps 8..11 read the accumulators back
+// (tcgen05.ld: warp w reads lanes 32 (w % 4) .. + 31) chain after chain and
+// write the result. Stages and accumulators are handed over with mbarriers;
+// every wait is bounded: a wait that gives up sets the error word, and the
+// kernel finishes without further MMAs.
 //
 // The small steps (LU with partial pivoting of G, the QR of Y by shifted
 // Cholesky QR, the SVD of the small matrix Q* A) run in FP64 in plain CUDA
@@ -53,11 +54,18 @@ namespace oocpca {
 constexpr int kTileM = 128;  // rows of an MMA tile (tensor-memory lanes)
 constexpr int kTileN = 64;   // columns of the accumulator (l <= 64)
 constexpr int kStageK = 32;  // K of one pipeline stage: 32 FP32 = one 128-byte swizzle row
-constexpr int kThreads = 256;
-constexpr int kStages = 3;
+constexpr int kThreads = 384;
+template <int MODE> struct Stages;  // pipeline depth per mode (shared memory: 192 KB each)
 constexpr int kConvWarpFirst = 2;  // converter warps 2..7
 constexpr int kConvWarps = 6;
-constexpr int kEpiWarpFirst = 4;   // epilogue warps 4..7
+constexpr int kEpiWarpFirst = 8;   // epilogue warps 8..11 (warp % 4 = tensor-memory lane quarter)
+// The tensor cores' FP32 accumulator does not round each addition to
+// nearest, so a long chain of MMAs into one accumulator drifts by up to
+// about 2^-24 per added term (measured: 4e-4 of sigma_1 with K = 30,000).
+// A chain therefore covers kChainStages stages (256 K-elements); the
+// epilogue warps add every chain's accumulator into registers (FP32, round
+// to nearest) while the next chain runs in the other of two accumulators.
+constexpr int kChainStages = 8;
 constexpr unsigned kWaitLimit = 1u << 22;  // polls of one mbarrier wait before it gives up
 
 enum : int { kErrNone = 0, kErrTimeout = 1 };
@@ -216,6 +224,9 @@ struct GemmArgs {
     int* err;            // error word (kErrTimeout)
 };
 
+template <> struct Stages<kModeAW> { static constexpr int value = 4; };   // 48 KB per stage
+template <> struct Stages<kModeATY> { static constexpr int value = 3; };  // 64 KB per stage
+
 template <int MODE>
 struct StageLayout {
     // G1: raw A (TF32 head in place) | A tail | B head | B tail
@@ -229,7 +240,7 @@ struct StageLayout {
     static constexpr uint32_t blo = bhi + kB;
     static constexpr uint32_t bytes = blo + kB;
     static constexpr uint32_t tx = kA + 2 * kB;              // bytes the TMA delivers per stage
-    static constexpr uint32_t smem = kStages * bytes + 1024; // + alignment slack
+    static constexpr uint32_t smem = Stages<MODE>::value * bytes + 1024; // + alignment slack
 };
 
 template <int MODE>
@@ -237,11 +248,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 pca_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
                 const __grid_constant__ CUtensorMap mapBl, GemmArgs g) {
     using SL = StageLayout<MODE>;
+    constexpr int kStages = Stages<MODE>::value;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[kStages], conv_bar[kStages], empty_bar[kStages];
-    __shared__ __align__(8) uint64_t accum_bar;
+    __shared__ __align__(8) uint64_t full_bar[4], conv_bar[4], empty_bar[4];
+    __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
     __shared__ uint32_t s_tmem;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
@@ -258,6 +270,7 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const int kend = min(g.rows, kbeg + g.k_stages * kStageK);
         nk = kend > kbeg ? (kend - kbeg + kStageK - 1) / kStageK : 0;
     }
+    const int nchains = (nk + kChainStages - 1) / kChainStages;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -265,13 +278,16 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             mbar_init(smem_u32(&conv_bar[s]), kConvWarps);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&accum_bar), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull_bar[b]), 1);
+            mbar_init(smem_u32(&tempty_bar[b]), 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_shared();
     }
-    if (warp == 1) {  // tensor memory: 64 columns x 128 lanes of FP32 accumulator
+    if (warp == 1) {  // tensor memory: two accumulators of 64 columns x 128 lanes (FP32)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&s_tmem)), "r"(kTileN) : "memory");
+                     ::"r"(smem_u32(&s_tmem)), "r"(2 * kTileN) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
@@ -309,9 +325,15 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
+            int committed = -1;  // last chain committed
             for (int i = 0; i < nk; ++i) {
                 const int s = i % kStages;
                 const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+                const int c = i / kChainStages, b = c & 1;
+                if (i % kChainStages == 0) {  // a new chain: its accumulator must have been read
+                    if (!mbar_wait(smem_u32(&tempty_bar[b]), ((uint32_t)(c >> 1) & 1u) ^ 1u, g.err)) break;
+                    tc_fence_after();
+                }
                 if (!mbar_wait(smem_u32(&conv_bar[s]), ph, g.err)) break;
                 tc_fence_after();
                 const unsigned char* st = smem + s * SL::bytes;
@@ -319,20 +341,26 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
                 const uint64_t al = sw128_desc(smem_u32(st + SL::lo));
                 const uint64_t bh = sw128_desc(smem_u32(st + SL::bhi));
                 const uint64_t bl = sw128_desc(smem_u32(st + SL::blo));
+                const uint32_t acc = tmem + (uint32_t)(b * kTileN);
+                const uint32_t first = (i % kChainStages) == 0;
 #pragma unroll
                 for (int kk = 0; kk < kStageK / 8; ++kk) {  // K = 8 per MMA: 32 bytes = 2 in the address field
                     const uint64_t o = (uint64_t)(2 * kk);
-                    mma_tf32(tmem, ah + o, bh + o, (i | kk) != 0);
-                    mma_tf32(tmem, ah + o, bl + o, 1u);
-                    mma_tf32(tmem, al + o, bh + o, 1u);
+                    mma_tf32(acc, ah + o, bh + o, (first && kk == 0) ? 0u : 1u);
+                    mma_tf32(acc, ah + o, bl + o, 1u);
+                    mma_tf32(acc, al + o, bh + o, 1u);
                 }
                 mma_commit(smem_u32(&empty_bar[s]));  // the stage is free once these MMAs are done
+                if (i % kChainStages == kChainStages - 1 || i == nk - 1) {
+                    mma_commit(smem_u32(&tfull_bar[b]));  // the chain's accumulator is complete
+                    committed = c;
+                }
             }
-            mma_commit(smem_u32(&accum_bar));
-            // the accumulator must be complete before the tensor memory is released
-            mbar_wait_drain(smem_u32(&accum_bar), 0);
+            // the MMAs must be complete before the tensor memory is released
+            if (committed >= 0)
+                mbar_wait_drain(smem_u32(&tfull_bar[committed & 1]), (uint32_t)(committed >> 1) & 1u);
         }
-    } else {
+    } else if (warp < kEpiWarpFirst) {
         // converters: TF32 head / tail of the A tile (G2: transposed to K-major)
         const int ct = threadIdx.x - kConvWarpFirst * 32;  // 0 .. 191
         for (int i = 0; i < nk; ++i) {
@@ -357,57 +385,77 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
                 const unsigned char* raw = st + SL::raw;
                 unsigned char* hi = st + SL::hi;
                 unsigned char* lo = st + SL::lo;
-                for (int e = ct; e < kTileM * kStageK; e += kConvWarps * 32) {
-                    const int c = e % 32, k = (e / 32) % 32, q = e / 1024;
-                    const float x = *reinterpret_cast<const float*>(raw + q * 4096 + sw128_offset(k, c));
-                    const float h = tf32_head(x);
-                    const uint32_t o = sw128_offset(32 * q + c, k);
-                    *reinterpret_cast<float*>(hi + o) = h;
-                    *reinterpret_cast<float*>(lo + o) = x - h;
+                // a thread takes 4 consecutive rows k0..k0+3 of one column: 4 loads,
+                // one 16-byte store of head and of tail (a chunk of the K-major row)
+                for (int e = ct; e < kTileM * kStageK / 4; e += kConvWarps * 32) {
+                    const int c = e % 32, k0 = ((e / 32) % 8) * 4, q = e / 256;
+                    const unsigned char* box = raw + q * 4096;
+                    float4 x, h, t;
+                    x.x = *reinterpret_cast<const float*>(box + sw128_offset(k0, c));
+                    x.y = *reinterpret_cast<const float*>(box + sw128_offset(k0 + 1, c));
+                    x.z = *reinterpret_cast<const float*>(box + sw128_offset(k0 + 2, c));
+                    x.w = *reinterpret_cast<const float*>(box + sw128_offset(k0 + 3, c));
+                    h.x = tf32_head(x.x); t.x = x.x - h.x;
+                    h.y = tf32_head(x.y); t.y = x.y - h.y;
+                    h.z = tf32_head(x.z); t.z = x.z - h.z;
+                    h.w = tf32_head(x.w); t.w = x.w - h.w;
+                    const uint32_t o = sw128_offset(32 * q + c, k0);  // 16-byte aligned: k0 % 4 == 0
+                    *reinterpret_cast<float4*>(hi + o) = h;
+                    *reinterpret_cast<float4*>(lo + o) = t;
                 }
             }
             fence_async_shared();  // generic-proxy writes become visible to the tensor cores
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&conv_bar[s]));
         }
-        if (warp >= kEpiWarpFirst && mbar_wait(smem_u32(&accum_bar), 0, g.err)) {
+    } else {
+        // epilogue: add each chain's accumulator (FP32, round to nearest), then write
+        const int q = warp % 4;                            // tensor-memory lanes 32 q .. 32 q + 31
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+        float v[kTileN];
+#pragma unroll
+        for (int c = 0; c < kTileN; ++c) v[c] = 0.0f;
+        bool ok = true;
+        for (int c = 0; c < nchains; ++c) {
+            const int b = c & 1;
+            if (!mbar_wait(smem_u32(&tfull_bar[b]), (uint32_t)(c >> 1) & 1u, g.err)) { ok = false; break; }
             tc_fence_after();
-            const int q = warp - kEpiWarpFirst;               // tensor-memory lanes 32 q .. 32 q + 31
-            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16);
-            const int r = m0 + 32 * q + lane;                 // G1: row of A; G2: column of A
-            float v[kTileN];
 #pragma unroll
-            for (int c = 0; c < kTileN; c += 16) {
+            for (int cc = 0; cc < kTileN; cc += 16) {
                 float t[16];
-                tmem_ld16(taddr + (uint32_t)c, t);
+                tmem_ld16(lane_addr + (uint32_t)(b * kTileN + cc), t);
 #pragma unroll
-                for (int u = 0; u < 16; ++u) v[c + u] = nk > 0 ? t[u] : 0.0f;  // no K: a zero product
+                for (int u = 0; u < 16; ++u) v[cc + u] += t[u];
             }
-            if (MODE == kModeAW) {
-                if (r < g.rows) {
-                    const int64_t col = (int64_t)g.row_offset + r;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[b]));
+        }
+        const int r = m0 + 32 * q + lane;                  // G1: row of A; G2: column of A
+        if (ok && MODE == kModeAW) {
+            if (r < g.rows) {
+                const int64_t col = (int64_t)g.row_offset + r;
 #pragma unroll
-                    for (int j = 0; j < kTileN; ++j) {
-                        const float y = g.shift ? v[j] - g.shift[j] : v[j];
-                        const float h = tf32_head(y);
-                        g.yt[j * g.ldy + col] = y;
-                        g.yt_hi[j * g.ldy + col] = h;
-                        g.yt_lo[j * g.ldy + col] = y - h;
-                    }
+                for (int j = 0; j < kTileN; ++j) {
+                    const float y = g.shift ? v[j] - g.shift[j] : v[j];
+                    const float h = tf32_head(y);
+                    g.yt[j * g.ldy + col] = y;
+                    g.yt_hi[j * g.ldy + col] = h;
+                    g.yt_lo[j * g.ldy + col] = y - h;
                 }
-            } else if (r < g.cols) {
-                float4* dst = reinterpret_cast<float4*>(g.gpart + ((int64_t)split * g.cols + r) * kTileN);
-#pragma unroll
-                for (int j = 0; j < kTileN / 4; ++j)
-                    dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
             }
+        } else if (ok && r < g.cols) {
+            float4* dst = reinterpret_cast<float4*>(g.gpart + ((int64_t)split * g.cols + r) * kTileN);
+#pragma unroll
+            for (int j = 0; j < kTileN / 4; ++j)
+                dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTileN)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTileN)
                      : "memory");
     }
 }

@@ -300,8 +300,9 @@ def low_rank_matrix(m: int, n: int, rank: int, seed: int, sigma=None, noise: flo
         return A, sigma, U0, V0
     g = torch.Generator(device=device)
     g.manual_seed(seed)
-    U0, _ = torch.linalg.qr(torch.randn(m, rank, generator=g, device=device, dtype=torch.float64))
-    V0, _ = torch.linalg.qr(torch.randn(n, rank, generator=g, device=device, dtype=torch.float64))
+    # orthonormal factors by numpy's QR on the host (m x rank and n x rank are small)
+    U0 = torch.as_tensor(np.linalg.qr(rng.standard_normal((m, rank)))[0], device=device)
+    V0 = torch.as_tensor(np.linalg.qr(rng.standard_normal((n, rank)))[0], device=device)
     s = torch.as_tensor(sigma, device=device)
     dt = dtype or torch.float32
     A = torch.empty((m, n), device=device, dtype=dt)
