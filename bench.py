@@ -674,10 +674,15 @@ def run_served_only(a):
 def run_affinity(a):
     """--workload affinity: P from X on the GPU (exact kNN k = 90, perplexity
     30, symmetrisation) for the N = 1M, D = 50 mixture of n1m_2d (rank 0 only).
-    The roofline line is the kNN kernel's: 3 flops (subtract, multiply, add)
-    per pair and dimension over N (N - 1) D against the FP32 lanes' rate for
-    that mix (152 SMs x 128 lanes x 1.5 flops per instruction x the sampled
-    SM clock)."""
+    The roofline line is the kNN's. With the tensor-core kNN (the default at
+    this size): 2 N (N - 1) D flops (one multiply-add per pair and
+    dimension of the products the distances need) against the TF32 dense
+    peak; the kernel issues 3 MMAs per K-step (head and tail terms) over D
+    padded to a multiple of 8, so its ceiling is D / (3 * 8 ceil(D / 8)) of
+    that peak (0.30 at D = 50). With the FP32-lane kernels: 3 flops
+    (subtract, multiply, add) per pair and dimension over N (N - 1) D against
+    the FP32 lanes' rate for that mix (152 SMs x 128 lanes x 1.5 flops per
+    instruction x the sampled SM clock)."""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
@@ -708,6 +713,7 @@ def run_affinity(a):
         wall = time.perf_counter() - t0
         clocks = sampler.stop()
         launches = aff.launch_count() - launches0
+        knn_info = aff.knn_info()
         nnz = P.nnz
         # end to end: X from pinned host memory, P back to pinned host memory
         Xh = torch.from_numpy(X).pin_memory()
@@ -727,17 +733,25 @@ def run_affinity(a):
     ms = {kk: statistics.median(ph[kk] for ph in phases) for kk in phases[0]}
     total_ms = sum(ms.values())
     clk = clocks.get("sm_mhz") or 2070.0
-    peak = 152 * 128 * 1.5 * clk * 1e6 / 1e12  # TFLOP/s for the sub + fma mix
-    achieved = 3.0 * N * (N - 1) * D / (ms["knn"] * 1e-3) / 1e12
+    if knn_info["kernel"] == "tc":
+        peak, basis = peak_tensor_tf32()
+        achieved = 2.0 * N * (N - 1) * D / (ms["knn"] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_basis": basis + " (TF32 dense)",
+                "ceiling_3xtf32": D / (3 * 8 * ((D + 7) // 8))}
+    else:
+        peak = 152 * 128 * 1.5 * clk * 1e6 / 1e12  # TFLOP/s for the sub + fma mix
+        achieved = 3.0 * N * (N - 1) * D / (ms["knn"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_basis": f"152 SMs x 128 FP32 lanes x 1.5 flop/instr x {clk:.0f} MHz (sampled)"}
     line = {"metric": "affinity builds/s (exact kNN k=90, perplexity 30, N=1M, D=50)",
             "value": 1e3 / total_ms, "unit": "builds/s", "n_gpus": 1, "steps": steps, "warmup": warm,
             "ms_per_step": total_ms, "higher_is_better": True, "dtype": "f32 (kNN), f64 (bandwidths)",
             "data": "synthetic", "config": {"workload": f"N={N} 50-d mixture (100 clusters + 5% background), "
                                                       "k=90, perplexity 30", "l2": "inputs larger than L2"},
             "phases_ms": ms, "nnz": nnz, "wall_s_per_step": wall / steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_basis": f"152 SMs x 128 FP32 lanes x 1.5 flop/instr x {clk:.0f} MHz (sampled)"},
+            "knn": knn_info, "roofline": roof,
             "e2e": {"value": steps / e2e_wall, "unit": "builds/s", "h2d_bytes_per_step": X.nbytes,
                     "d2h_bytes_per_step": 4 * (N + 1) + 8 * nnz},
             "gpu_launches": launches, "clocks": clocks}

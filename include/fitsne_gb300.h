@@ -454,10 +454,15 @@ void* tsne_batch_stream(const tsne_batch* batch);
  * neighbours (1..256, k < N, 2 N k < 2^31); all device memory (about
  * 40 N k bytes) is allocated here; work is enqueued on stream (cudaStream_t,
  * NULL = legacy default). INVALID_ARG on bad sizes, OOM. The kNN kernel is
- * chosen here: the register-tiled one for N >= 400,000 where its shared
- * memory (D, k) fits, else the one-candidate-per-lane one; the environment
- * variable FITSNE_KNN_KERNEL=tiled or =rows, read at create, overrides the
- * size rule (both give the same lists and distances, bit for bit).
+ * chosen here: from N = 32,768 the tensor-core one (tcgen05 tiles of
+ * 128 x 128 approximate distances shortlist the candidates; the shortlist
+ * gets the exact FP32 distances; queries whose shortlist is not provably
+ * complete are recomputed by the row kernel; about 14 MB per 1,000 points
+ * more device memory); below it the register-tiled one for N >= 400,000
+ * where its shared memory (D, k) fits (never, with the default threshold),
+ * else the one-candidate-per-lane one. The environment variable
+ * FITSNE_KNN_KERNEL=tc, =tiled or =rows, read at create, overrides the size
+ * rule (all three give the same lists and distances, bit for bit).
  * tsne_affinity_compute: X is DEVICE memory, N x D row-major FP32, read
  * only; 1 <= perplexity <= k. Writes into *P_out a CSR that points into the
  * workspace: valid until the next compute or destroy, owned by the
@@ -478,6 +483,12 @@ int tsne_affinity_knn_copy(const tsne_affinity* aff, int32_t* idx_host, float* d
 int tsne_affinity_phase_ms(const tsne_affinity* aff, double* ms_out);
 /* Kernels the workspace has launched (host-side count). */
 int64_t tsne_affinity_launch_count(const tsne_affinity* aff);
+/* The kNN kernel chosen at create (*kernel_out: 0 row kernel, 1 register-
+ * tiled, 2 tensor cores) and the number of queries of the last compute that
+ * the tensor-core kernel left to the row kernel (*recomputed_out; 0 for the
+ * other kernels). Either pointer may be NULL. INVALID_ARG on a NULL
+ * workspace. */
+int tsne_affinity_knn_info(const tsne_affinity* aff, int32_t* kernel_out, int64_t* recomputed_out);
 
 /*
  * t-SNE heatmaps (Sec. 5). A 1-D embedding y of N cells is cut into n_bins

@@ -30,7 +30,7 @@ __all__ = ["Plan", "DeviceCSR", "Schedule", "tsne_plan_create", "tsne_plan_destr
            "tsne_batch_set_tuning", "tsne_batch_get_tuning", "tsne_batch_autotune",
            "tsne_batch_launch_count", "tsne_batch_stream", "Affinity", "tsne_affinity_create",
            "tsne_affinity_destroy", "tsne_affinity_compute", "tsne_affinity_knn_copy",
-           "tsne_affinity_phase_ms", "tsne_affinity_launch_count", "Heatmap", "tsne_heatmap_create",
+           "tsne_affinity_phase_ms", "tsne_affinity_launch_count", "tsne_affinity_knn_info", "Heatmap", "tsne_heatmap_create",
            "tsne_heatmap_destroy", "tsne_heatmap_bin", "tsne_heatmap_nearest", "tsne_heatmap_phase_ms",
            "tsne_heatmap_launch_count", "OocPca", "tsne_oocpca_create", "tsne_oocpca_destroy",
            "tsne_oocpca_run", "tsne_oocpca_debug_copy", "tsne_oocpca_phase_ms",
@@ -286,6 +286,15 @@ def tsne_affinity_launch_count(aff) -> int:
     return lib().tsne_affinity_launch_count(aff)
 
 
+def tsne_affinity_knn_info(aff) -> tuple[int, int]:
+    """(kNN kernel: 0 rows, 1 tiled, 2 tensor cores; queries of the last
+    compute recomputed by the row kernel)."""
+    kind = ctypes.c_int32()
+    rec = ctypes.c_int64()
+    check(lib().tsne_affinity_knn_info(aff, ctypes.byref(kind), ctypes.byref(rec)))
+    return kind.value, rec.value
+
+
 class Affinity:
     """Workspace for P from data X (N x D float32 on the device): exact kNN,
     perplexity calibration and symmetrisation in the library's kernels.
@@ -323,6 +332,12 @@ class Affinity:
     def phase_ms(self) -> dict:
         """Device time of the last compute's phases (CUDA events on its stream)."""
         return dict(zip(("knn", "bandwidths", "edge_sort", "symmetrise"), tsne_affinity_phase_ms(self._h)))
+
+    def knn_info(self) -> dict:
+        """The kNN kernel in use ("rows", "tiled", "tc") and the queries of the
+        last compute that the tensor-core kernel left to the row kernel."""
+        kind, rec = tsne_affinity_knn_info(self._h)
+        return {"kernel": ("rows", "tiled", "tc")[kind], "recomputed": rec}
 
     def close(self):
         if self._h is not None:

@@ -151,6 +151,7 @@ _SIGNATURES = [
     ("tsne_affinity_knn_copy", ctypes.c_int, [_P, _P, _P, _P]),
     ("tsne_affinity_phase_ms", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("tsne_affinity_launch_count", ctypes.c_int64, [_P]),
+    ("tsne_affinity_knn_info", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     ("tsne_heatmap_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
                                            ctypes.POINTER(_P)]),
     ("tsne_heatmap_destroy", ctypes.c_int, [_P]),

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfitsne_gb300.so")
 SOURCES = ["fitsne_abi.cu", "fitsne_kernels.cu", "fitsne_fft.cu", "fitsne_noalloc.cu", "fitsne_affinity.cu",
-           "fitsne_reorder.cu", "fitsne_batch.cu", "fitsne_heatmap.cu", "fitsne_oocpca.cu"]
+           "fitsne_reorder.cu", "fitsne_batch.cu", "fitsne_heatmap.cu", "fitsne_oocpca.cu",
+           "fitsne_knn_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

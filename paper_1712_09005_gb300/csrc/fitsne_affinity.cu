@@ -97,10 +97,14 @@ __device__ __forceinline__ void knn_insert(float* ld, int* li, int k, float d, i
 
 // Exact k nearest neighbours of queries [q0, q0 + nq) among all N points
 // (self excluded). X is N x D row-major. Output sorted by (d^2, index).
+// With kList the queries are qlist[q0 .. q0 + nq) instead (the queries the
+// tensor-core kNN leaves to this kernel).
+template <bool kList>
 __global__ void __launch_bounds__(kKnnWarps * 32)
 knn_kernel(const float* __restrict__ X, int64_t N, int D, int k, int64_t q0, int64_t nq,
-           int32_t* __restrict__ out_idx, float* __restrict__ out_d2) {
+           int32_t* __restrict__ out_idx, float* __restrict__ out_d2, const int32_t* __restrict__ qlist) {
     extern __shared__ float sm[];
+    __shared__ int64_t s_id[kKnnWarps * kKnnQ];  // query of each slot (kList), -1 past the end
     const int Ds = knn_stride(D);
     float* s_c = sm;                                     // [kKnnTile][Ds]
     float* s_q = s_c + kKnnTile * Ds;                    // [kKnnWarps * kKnnQ][Ds]
@@ -111,10 +115,16 @@ knn_kernel(const float* __restrict__ X, int64_t N, int D, int k, int64_t q0, int
     for (int64_t qb = blockIdx.x; qb < nqb; qb += gridDim.x) {
         const int64_t qbase = q0 + qb * kKnnWarps * kKnnQ;
         __syncthreads();
+        if (kList && threadIdx.x < kKnnWarps * kKnnQ) {
+            const int64_t p = qbase + threadIdx.x;
+            s_id[threadIdx.x] = p < q0 + nq ? (int64_t)qlist[p] : -1;
+        }
+        if (kList) __syncthreads();
         for (int t = threadIdx.x; t < kKnnWarps * kKnnQ * Ds; t += blockDim.x) {
             const int q = t / Ds, d = t - q * Ds;
-            const int64_t gq = qbase + q;
-            s_q[t] = (d < D && gq < q0 + nq) ? X[gq * D + d] : 0.0f;
+            const int64_t p = qbase + q;
+            const int64_t gq = kList ? s_id[q] : p;
+            s_q[t] = (d < D && p < q0 + nq) ? X[gq * D + d] : 0.0f;
         }
         for (int t = threadIdx.x; t < kKnnWarps * kKnnQ * k; t += blockDim.x) {
             s_ld[t] = INFINITY;
@@ -155,8 +165,9 @@ knn_kernel(const float* __restrict__ X, int64_t N, int D, int k, int64_t q0, int
                     // a non-finite distance ranks as +inf (by index among
                     // equals), so every list fills with valid indices
                     if (!(acc[u] <= 3.402823466e38f)) acc[u] = INFINITY;
-                    const int64_t gq = qbase + wid * kKnnQ + u;
-                    const bool ok = gc < N && gq < q0 + nq && gc != gq;
+                    const int64_t p = qbase + wid * kKnnQ + u;
+                    const int64_t gq = kList ? s_id[wid * kKnnQ + u] : p;
+                    const bool ok = gc < N && p < q0 + nq && gc != gq;
                     const int ci = (int)gc;
                     const bool take = ok && knn_less(acc[u], ci, thr[u], thi[u]);
                     unsigned m = __ballot_sync(kFullA, take);
@@ -179,8 +190,9 @@ knn_kernel(const float* __restrict__ X, int64_t N, int D, int k, int64_t q0, int
         __syncthreads();
         for (int t = threadIdx.x; t < kKnnWarps * kKnnQ * k; t += blockDim.x) {
             const int q = t / k, m = t - q * k;
-            const int64_t gq = qbase + q;
-            if (gq < q0 + nq) {
+            const int64_t p = qbase + q;
+            const int64_t gq = kList ? s_id[q] : p;
+            if (p < q0 + nq) {
                 out_idx[gq * k + m] = s_li[t];
                 out_d2[gq * k + m] = s_ld[t];
             }
@@ -204,6 +216,9 @@ constexpr int kTileC = 128;
 // (sorted insertions between two barriers, 8 warps per SM) costs about the
 // same per query at any N, while the distances cost O(N) per query, so the
 // row kernel (16 warps per SM hide the insertions) wins on small N.
+#ifndef FITSNE_KNN_TC_MIN_N
+#define FITSNE_KNN_TC_MIN_N 32768
+#endif
 #ifndef FITSNE_KNN_TILED_MIN_N
 #define FITSNE_KNN_TILED_MIN_N 400000
 #endif
@@ -691,7 +706,9 @@ struct tsne_affinity {
     int sm_count = 0;
     cudaStream_t stream = nullptr;
     int max_smem = 0;             // opt-in shared memory per block
-    bool tiled = false;           // knn_tiled_kernel fits (else knn_kernel)
+    int knn_kind = 0;             // 0 knn_kernel, 1 knn_tiled_kernel, 2 tensor cores (+ knn_kernel)
+    fitsne::KnnTc* tc = nullptr;  // workspace of the tensor-core kNN
+    int64_t recomputed = 0;       // queries of the last compute left to knn_kernel
     int64_t Np = 0;               // N rounded up to the candidate tile
     float* Xt = nullptr;          // [D][Np] transposed, zero-padded X
     int32_t* knn_idx = nullptr;   // [N k]
@@ -729,6 +746,7 @@ void free_affinity(tsne_affinity* a) {
         if (p) cudaFree(p);
     for (cudaEvent_t e : a->ev)
         if (e) cudaEventDestroy(e);
+    fitsne::knn_tc_destroy(a->tc);
     delete a;
 }
 
@@ -773,18 +791,23 @@ int tsne_affinity_create(int64_t N, int32_t D, int32_t k, void* stream, tsne_aff
     for (int e = 0; e < 5 && ce == cudaSuccess; ++e) ce = cudaEventCreate(&a->ev[e]);
     if (ce != cudaSuccess) { free_affinity(a); return aff_cuda_fail(ce, "device setup"); }
     const int64_t nblocks = (nk + fitsne::kRadixTile - 1) / fitsne::kRadixTile;
-    // kernel choice: the tiled kernel where its shared memory fits and N is
-    // large; FITSNE_KNN_KERNEL=tiled|rows in the environment overrides the
-    // size rule (tests and tuning; "tiled" still needs the memory to fit)
+    // kernel choice: the tensor-core kernel from N = FITSNE_KNN_TC_MIN_N;
+    // below it the tiled kernel where its shared memory fits and N is large,
+    // else the row kernel. FITSNE_KNN_KERNEL=tc|tiled|rows in the
+    // environment overrides the size rule (tests and tuning; "tiled" still
+    // needs the memory to fit)
     const bool fits = fitsne::knn_tiled_smem_bytes(D, k) <= (size_t)a->max_smem;
-    a->tiled = fits && N >= FITSNE_KNN_TILED_MIN_N;
+    const bool tc_ok = fitsne::knn_tc_supported(D, k);
+    a->knn_kind = (tc_ok && N >= FITSNE_KNN_TC_MIN_N) ? 2 : (fits && N >= FITSNE_KNN_TILED_MIN_N) ? 1 : 0;
     if (const char* ov = getenv("FITSNE_KNN_KERNEL")) {
-        if (!strcmp(ov, "tiled")) a->tiled = fits;
-        else if (!strcmp(ov, "rows")) a->tiled = false;
+        if (!strcmp(ov, "tc")) a->knn_kind = tc_ok ? 2 : 0;
+        else if (!strcmp(ov, "tiled")) a->knn_kind = fits ? 1 : 0;
+        else if (!strcmp(ov, "rows")) a->knn_kind = 0;
     }
     a->Np = (N + fitsne::kTileC - 1) / fitsne::kTileC * fitsne::kTileC;
     int rc = TSNE_OK;
-    if (a->tiled) rc = aff_alloc(&a->Xt, (size_t)D * (size_t)a->Np, "transposed X");
+    if (a->knn_kind == 1) rc = aff_alloc(&a->Xt, (size_t)D * (size_t)a->Np, "transposed X");
+    if (!rc && a->knn_kind == 2) rc = fitsne::knn_tc_create(N, D, k, a->sm_count, &a->tc);
     if (!rc) rc = aff_alloc(&a->knn_idx, (size_t)nk, "kNN indices");
     if (!rc) rc = aff_alloc(&a->knn_d2, (size_t)nk, "kNN distances");
     if (!rc) rc = aff_alloc(&a->pc, (size_t)nk, "conditional affinities");
@@ -823,7 +846,26 @@ int tsne_affinity_compute(tsne_affinity* a, const float* X, double perplexity, t
     a->nnz = -1;
     ACU(cudaEventRecord(a->ev[0], st), "event");
     // 1. exact kNN
-    if (a->tiled) {
+    a->recomputed = 0;
+    if (a->knn_kind == 2) {
+        if (int rc = knn_tc_launch(a->tc, X, a->knn_idx, a->knn_d2, st, &a->launches)) return rc;
+        int64_t left = 0;
+        const int32_t* list = nullptr;
+        if (int rc = knn_tc_leftover(a->tc, st, &left, &list)) return rc;
+        a->recomputed = left;
+        if (left > 0) {
+            const int64_t nqb = (left + kKnnWarps * kKnnQ - 1) / (kKnnWarps * kKnnQ);
+            const int grid = (int)std::min<int64_t>(nqb, 64LL * a->sm_count);
+            ACU(cudaFuncSetAttribute(knn_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)knn_smem_bytes(a->D, k)),
+                "kNN shared memory");
+            knn_kernel<true><<<grid, kKnnWarps * 32, knn_smem_bytes(a->D, k), st>>>(
+                X, N, a->D, k, 0, left, a->knn_idx, a->knn_d2, list);
+            ACU(cudaGetLastError(), "kNN launch");
+            a->launches += 1;
+        }
+        a->launches -= 1;  // the count below includes one kNN kernel
+    } else if (a->knn_kind == 1) {
         const int64_t total = (int64_t)a->D * a->Np;
         transpose_pad_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 8LL * a->sm_count), 256, 0, st>>>(
             X, N, a->D, a->Np, a->Xt);
@@ -839,11 +881,11 @@ int tsne_affinity_compute(tsne_affinity* a, const float* X, double perplexity, t
         const int64_t nqb = (N + kKnnWarps * kKnnQ - 1) / (kKnnWarps * kKnnQ);
         const int grid = (int)std::min<int64_t>(nqb, 64LL * a->sm_count);
         // a per-function attribute: set for this workspace's size at each launch
-        ACU(cudaFuncSetAttribute(knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        ACU(cudaFuncSetAttribute(knn_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)knn_smem_bytes(a->D, k)),
             "kNN shared memory");
-        knn_kernel<<<grid, kKnnWarps * 32, knn_smem_bytes(a->D, k), st>>>(X, N, a->D, k, 0, N, a->knn_idx,
-                                                                           a->knn_d2);
+        knn_kernel<false><<<grid, kKnnWarps * 32, knn_smem_bytes(a->D, k), st>>>(X, N, a->D, k, 0, N,
+                                                                                  a->knn_idx, a->knn_d2, nullptr);
         ACU(cudaGetLastError(), "kNN launch");
     }
     ACU(cudaEventRecord(a->ev[1], st), "event");
@@ -929,5 +971,13 @@ int tsne_affinity_phase_ms(const tsne_affinity* a, double* ms_out) {
 }
 
 int64_t tsne_affinity_launch_count(const tsne_affinity* a) { return a ? a->launches : 0; }
+
+int tsne_affinity_knn_info(const tsne_affinity* a, int32_t* kernel_out, int64_t* recomputed_out) {
+    fitsne::clear_error();
+    if (!a) return fitsne::set_error(TSNE_ERR_INVALID_ARG, "affinity object is NULL");
+    if (kernel_out) *kernel_out = a->knn_kind;
+    if (recomputed_out) *recomputed_out = a->recomputed;
+    return TSNE_OK;
+}
 
 }  // extern "C"

@@ -454,4 +454,18 @@ cudaError_t launch_validate(const tsne_csr& P, int64_t N, int32_t* flag, int sm_
                             cudaStream_t st);
 cudaError_t launch_fill(float* a, float v, int64_t n, int sm_count, cudaStream_t st);
 
+// Exact kNN with the distance tiles on the tensor cores (fitsne_knn_tc.cu):
+// lists and distances bit for bit those of knn_kernel; queries whose
+// shortlist cannot be proved complete are listed for knn_kernel.
+struct KnnTc;
+bool knn_tc_supported(int D, int k);
+int knn_tc_create(int64_t N, int D, int k, int sm_count, KnnTc** out);
+void knn_tc_destroy(KnnTc* w);
+// Enqueues the pass over X (N x D device, FP32) on st; *launches += kernels.
+int knn_tc_launch(KnnTc* w, const float* X, int32_t* out_idx, float* out_d2, cudaStream_t st,
+                  int64_t* launches);
+// Synchronises st, then: the queries left to the row kernel (count, device
+// list). TSNE_ERR_TIMEOUT if a pipeline wait of the pass gave up.
+int knn_tc_leftover(KnnTc* w, cudaStream_t st, int64_t* count, const int32_t** list);
+
 }  // namespace fitsne

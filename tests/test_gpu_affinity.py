@@ -42,9 +42,9 @@ def _built():
     __graft_entry__.build()
 
 
-@pytest.fixture(params=["tiled", "rows"])
+@pytest.fixture(params=["tc", "tiled", "rows"])
 def knn_kernel(request, monkeypatch):
-    """Both kNN kernels on every case (the library picks by N otherwise:
+    """Every kNN kernel on every case (the library picks by N otherwise:
     the small cases here would all take the row kernel)."""
     monkeypatch.setenv("FITSNE_KNN_KERNEL", request.param)
     return request.param
