@@ -457,8 +457,9 @@ void* tsne_batch_stream(const tsne_batch* batch);
  * chosen here: from N = 32,768 the tensor-core one (tcgen05 tiles of
  * 128 x 128 approximate distances shortlist the candidates; the shortlist
  * gets the exact FP32 distances; queries whose shortlist is not provably
- * complete are recomputed by the row kernel; about 14 MB per 1,000 points
- * more device memory); below it the register-tiled one for N >= 400,000
+ * complete are recomputed by the row kernel; it needs about 1040 + 8 S
+ * bytes more device memory per point, S = 2 k + 32 rounded up to 64, 128,
+ * 256 or 512, plus 512 KB per SM); below it the register-tiled one for N >= 400,000
  * where its shared memory (D, k) fits (never, with the default threshold),
  * else the one-candidate-per-lane one. The environment variable
  * FITSNE_KNN_KERNEL=tc, =tiled or =rows, read at create, overrides the size
