@@ -304,10 +304,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapQH, const __grid_constant__
         tc_fence_after();
         if (warp == 0) {
             if (lane == 0 && !failed) {  // TMA producer
+                const int nkc = g.ksteps > 4 ? 2 : 1;  // 32-column chunks the K-steps read
                 const uint32_t qb = smem_u32(&q_full);
-                mbar_expect_tx(qb, 2 * kTile);
+                mbar_expect_tx(qb, 2 * nkc * kHalf);
                 for (int h = 0; h < 2; ++h)
-                    for (int kc = 0; kc < 2; ++kc)
+                    for (int kc = 0; kc < nkc; ++kc)
                         tma_load_2d(smem_u32(smem + kSmQ + h * kTile + kc * kHalf), h ? &mapQL : &mapQH, kc * 32,
                                     qt * kQ, qb);
                 int64_t issued = it0;
@@ -320,9 +321,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapQH, const __grid_constant__
                     }
                     unsigned char* st = smem + kSmC + s * 2 * kTile;
                     const uint32_t fb = smem_u32(&c_full[s]);
-                    mbar_expect_tx(fb, 2 * kTile);
+                    mbar_expect_tx(fb, 2 * nkc * kHalf);
                     for (int h = 0; h < 2; ++h)
-                        for (int kc = 0; kc < 2; ++kc)
+                        for (int kc = 0; kc < nkc; ++kc)
                             tma_load_2d(smem_u32(st + h * kTile + kc * kHalf), h ? &mapCL : &mapCH, kc * 32,
                                         ct * kC, fb);
                     issued = it + 1;
@@ -442,12 +443,18 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapQH, const __grid_constant__
                             }
                         }
                         const int c0 = ct * kC + cc;
-                        // groups of 4 candidates: a warp-uniform test of the
-                        // group's minimum, then one per candidate
+                        // groups of 4 candidates: the warp votes on every
+                        // group's minimum first (independent), then visits
+                        // the groups some list takes from, candidate by candidate
+                        bool hit[kChunk / 4];
 #pragma unroll
                         for (int j4 = 0; j4 < kChunk / 4; ++j4) {
                             const float mn = fminf(fminf(v[4 * j4], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3]));
-                            if (__ballot_sync(kFull, mn <= lim)) {
+                            hit[j4] = __any_sync(kFull, mn <= lim);
+                        }
+#pragma unroll
+                        for (int j4 = 0; j4 < kChunk / 4; ++j4) {
+                            if (hit[j4]) {
 #pragma unroll
                                 for (int u = 0; u < 4; ++u) {
                                     const int j = 4 * j4 + u;
@@ -638,10 +645,13 @@ int knn_tc_create(int64_t N, int D, int k, int sm_count, KnnTc** out) {
     if (!rc) rc = tc_alloc(&w->counts, (size_t)N, "kNN shortlist sizes");
     if (!rc) rc = tc_alloc(&w->leftover, (size_t)N, "kNN leftover queries");
     if (!rc) {
-        int r2 = encode_map_f32_2d(&w->mapQH, w->Qh, w->Np, kDp, kDp, 32, kQ);
-        if (!r2) r2 = encode_map_f32_2d(&w->mapQL, w->Ql, w->Np, kDp, kDp, 32, kQ);
-        if (!r2) r2 = encode_map_f32_2d(&w->mapCH, w->Ch, w->Np, kDp, kDp, 32, kC);
-        if (!r2) r2 = encode_map_f32_2d(&w->mapCL, w->Cl, w->Np, kDp, kDp, 32, kC);
+        // the maps cover the Kp columns the K-steps read (boxes past them
+        // read zeros and move no data)
+        const int64_t Kp = std::max<int64_t>(32, 8 * ((D + w->fold + 7) / 8));
+        int r2 = encode_map_f32_2d(&w->mapQH, w->Qh, w->Np, Kp, kDp, 32, kQ);
+        if (!r2) r2 = encode_map_f32_2d(&w->mapQL, w->Ql, w->Np, Kp, kDp, 32, kQ);
+        if (!r2) r2 = encode_map_f32_2d(&w->mapCH, w->Ch, w->Np, Kp, kDp, 32, kC);
+        if (!r2) r2 = encode_map_f32_2d(&w->mapCL, w->Cl, w->Np, Kp, kDp, 32, kC);
         if (r2 < 0) rc = set_error(TSNE_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
         else if (r2) rc = set_error(TSNE_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", r2);
     }
