@@ -253,6 +253,23 @@ __device__ void pace_wait(const unsigned* pace, unsigned target, int* err) {
     atomicExch(err, kErrTimeout);
 }
 
+// The MMAs of one (query tile, candidate tile) pair: KS K-steps of 8, each
+// head x head + head x tail + tail x head into the accumulator. Unrolled with
+// a compile-time count: a loop with a run-time count issued the MMAs at half
+// the rate (65.4 ms against 80.8 ms for the kernel at N = 400k without
+// filtering).
+template <int KS>
+__device__ __forceinline__ void tile_mmas(uint32_t acc, uint64_t qh, uint64_t ql, uint64_t ch, uint64_t cl) {
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+        // K-step ks: chunk ks / 4 (16 KB apart), 32 bytes = 2 address units per step
+        const uint64_t o = (uint64_t)((ks >> 2) * (kHalf >> 4) + 2 * (ks & 3));
+        mma_tf32(acc, qh + o, ch + o, kIdesc, ks ? 1u : 0u);
+        mma_tf32(acc, qh + o, cl + o, kIdesc, 1u);
+        mma_tf32(acc, ql + o, ch + o, kIdesc, 1u);
+    }
+}
+
 // Shortlist bookkeeping: the self candidate (v = -|q|^2, the smallest) is
 // kept while collecting and dropped at the end, so the limits use the
 // (k + 1)-th smallest value (0-based rank k), which is at least the k-th
@@ -352,12 +369,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapQH, const __grid_constant__
                     const uint64_t ch = sw128_desc(smem_u32(st));
                     const uint64_t cl = sw128_desc(smem_u32(st + kTile));
                     const uint32_t acc = tmem + (uint32_t)(b * kC);
-                    for (int ks = 0; ks < g.ksteps; ++ks) {
-                        // K-step ks: chunk ks / 4 (16 KB apart), 32 bytes = 2 address units per step
-                        const uint64_t o = (uint64_t)((ks >> 2) * (kHalf >> 4) + 2 * (ks & 3));
-                        mma_tf32(acc, qh + o, ch + o, kIdesc, ks ? 1u : 0u);
-                        mma_tf32(acc, qh + o, cl + o, kIdesc, 1u);
-                        mma_tf32(acc, ql + o, ch + o, kIdesc, 1u);
+                    switch (g.ksteps) {  // fully unrolled sequences issue back to back
+                        case 1: tile_mmas<1>(acc, qh, ql, ch, cl); break;
+                        case 2: tile_mmas<2>(acc, qh, ql, ch, cl); break;
+                        case 3: tile_mmas<3>(acc, qh, ql, ch, cl); break;
+                        case 4: tile_mmas<4>(acc, qh, ql, ch, cl); break;
+                        case 5: tile_mmas<5>(acc, qh, ql, ch, cl); break;
+                        case 6: tile_mmas<6>(acc, qh, ql, ch, cl); break;
+                        case 7: tile_mmas<7>(acc, qh, ql, ch, cl); break;
+                        default: tile_mmas<8>(acc, qh, ql, ch, cl); break;
                     }
                     mma_commit(smem_u32(&c_empty[s]));
                     mma_commit(smem_u32(&tfull[b]));
