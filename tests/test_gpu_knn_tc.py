@@ -47,17 +47,24 @@ def same_as_rows(X, k, monkeypatch, max_recomputed=0):
     return info
 
 
-@pytest.mark.parametrize("N,D,k,seed", [
-    (3001, 50, 90, 1),    # several query and candidate tiles, ragged tail
-    (1537, 3, 30, 2),     # low dimension: one K-step
-    (2000, 64, 150, 3),   # D at its maximum, eight K-steps
-    (1000, 10, 256, 4),   # k at its maximum
-    (200, 33, 1, 5),      # k = 1, D just past one 32-column chunk
-    (91, 20, 90, 6),      # N = k + 1: every other point
+@pytest.mark.parametrize("N,D,k,seed,left", [
+    (3001, 50, 90, 1, 0),     # several query and candidate tiles, ragged tail
+    (1537, 3, 30, 2, 0),      # low dimension: one K-step
+    (2000, 64, 150, 3, 0),    # D at its maximum, eight K-steps, the norm added in FP32
+    (1000, 10, 256, 4, 0),    # k at its maximum
+    (200, 33, 1, 5, 0),       # k = 1, D just past one 32-column chunk
+    (91, 20, 90, 6, 0),       # N = k + 1: every other point
+    # D = 1: one K-step, the norm in column 1; coordinates up to ~15 give a
+    # band (6e-5 of the norms) wider than the neighbour spacing, so the final
+    # shortlists of the dense clusters overflow their 128-entry slots and go
+    # to the row kernel (still the same lists)
+    (3000, 1, 30, 13, 3000),
+    (2500, 63, 2, 14, 0),     # D = 63: the norm in the last column, eight K-steps
+    (2049, 56, 90, 15, 0),    # D = 56: with the norm column, 57 columns round up to 64
 ])
-def test_tc_equals_rows_on_mixtures(N, D, k, seed, monkeypatch):
+def test_tc_equals_rows_on_mixtures(N, D, k, seed, left, monkeypatch):
     X = inputs.mixture(N=N, n_clusters=7, dim=D, seed=seed)
-    same_as_rows(X, k, monkeypatch)
+    same_as_rows(X, k, monkeypatch, max_recomputed=left)
 
 
 def test_far_from_origin_is_centred(monkeypatch):
