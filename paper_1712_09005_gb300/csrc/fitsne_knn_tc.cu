@@ -244,8 +244,11 @@ struct Args {
 // sweep the candidates together and share them in L2. Thread 0 only; the
 // wait is bounded (the error word is set and the pacing dropped when it
 // gives up). No data passes between CTAs.
-__device__ void pace_wait(const unsigned* pace, unsigned target, int* err) {
-    for (unsigned it = 0; it < (1u << 23); ++it) {
+__device__ void pace_wait(const unsigned* pace, unsigned target, int nct, int* err) {
+    // at most about 16 us per candidate tile of a round (a round takes about
+    // 1.5 us per tile), and at least 2 s
+    const uint64_t limit = std::max<uint64_t>(1ull << 23, (uint64_t)nct * 64ull);
+    for (uint64_t it = 0; it < limit; ++it) {
         if (*(volatile const unsigned*)pace >= target) return;
         if ((it & 255u) == 255u && *(volatile int*)err) return;
         __nanosleep(256);
@@ -315,7 +318,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapQH, const __grid_constant__
         __syncthreads();  // the previous query tile is finished: its MMAs are complete
         if (qn > 0 && threadIdx.x == 0) {
             atomicAdd(g.pace, 1u);  // round qn - 1 done
-            pace_wait(g.pace, (unsigned)qn * gridDim.x, g.err);
+            pace_wait(g.pace, (unsigned)qn * gridDim.x, g.nct, g.err);
         }
         __syncthreads();
         tc_fence_after();
