@@ -372,8 +372,22 @@ knn_tiled_kernel(const float* __restrict__ Xt, int64_t N, int64_t Np, int D, int
 
 // Bisection on beta per row (warp per row), FP64, the oracle's rule; writes
 // p_{j|i} (FP64) over the row's k neighbours.
+//
+// Each step first evaluates H in FP32 (exponentials, sums, logarithm); only
+// when that value lies within 1e-5 + kCalibSlack of the target does the step
+// evaluate H in FP64 as above. kCalibSlack bounds |H_fp32 - H_fp64|: the
+// exponent -beta x_j carries 3 roundings (beta, x_j, the product) and expf 2
+// units, so each term e_j errs by at most e_j (|t_j| 1.8e-7 + 2.4e-7) with
+// t_j = beta x_j; summed over k <= 256 terms (e_0 = 1 bounds S from below)
+// log S errs by at most 6.4e-5 and beta mu by 4e-5 + 5.5 x 6.4e-5; the FP32
+// sums (256 terms) add 1.6e-5 each; about 5e-4 in all, and the slack keeps a
+// factor 4 over it. So every decision (stop, sharpen, flatten) is the one the
+// FP64 evaluation takes: the same path, the same beta, the same p_{j|i} bit
+// for bit, with FP64 only in the last steps. exact_only: FP64 at every step.
+constexpr double kCalibSlack = 2e-3;
+
 __global__ void calibrate_kernel(const float* __restrict__ d2, int64_t N, int k, double target,
-                                 double* __restrict__ pc) {
+                                 double* __restrict__ pc, int exact_only) {
     const int lane = threadIdx.x % 32;
     const int64_t nwarp = (int64_t)gridDim.x * blockDim.x / 32;
     constexpr int V = kKnnKMax / 32;
@@ -381,28 +395,53 @@ __global__ void calibrate_kernel(const float* __restrict__ d2, int64_t N, int k,
         const float* row = d2 + i * k;
         const double dmin = (double)row[0];  // the list is sorted: row[0] is the smallest
         double x[V];
+        float xf[V];
 #pragma unroll
         for (int t = 0; t < V; ++t) {
             const int m = lane + 32 * t;
             x[t] = m < k ? (double)row[m] - dmin : 0.0;
+            xf[t] = (float)x[t];
         }
         double beta = 1.0, lo = -INFINITY, hi = INFINITY;
         for (int it = 0; it < 200; ++it) {
-            double S = 0.0, W = 0.0;
+            double H = NAN;
+            if (!exact_only) {
+                const float bf = (float)beta;
+                float Sf = 0.0f, Wf = 0.0f;
 #pragma unroll
-            for (int t = 0; t < V; ++t) {
-                if (lane + 32 * t < k) {
-                    const double e = exp(-beta * x[t]);
-                    S += e;
-                    W += e > 0.0 ? e * x[t] : 0.0;  // x = inf: no 0 * inf
+                for (int t = 0; t < V; ++t) {
+                    if (lane + 32 * t < k) {
+                        const float e = expf(-bf * xf[t]);
+                        Sf += e;
+                        Wf += e > 0.0f ? e * xf[t] : 0.0f;
+                    }
                 }
-            }
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-                S += __shfl_xor_sync(kFullA, S, o);
-                W += __shfl_xor_sync(kFullA, W, o);
+                for (int o = 16; o >= 1; o >>= 1) {
+                    Sf += __shfl_xor_sync(kFullA, Sf, o);
+                    Wf += __shfl_xor_sync(kFullA, Wf, o);
+                }
+                H = (double)(logf(Sf) + bf * (Wf / Sf));
             }
-            const double H = log(S) + beta * (W / S);
+            if (!(fabs(H - target) > 1e-5 + kCalibSlack)) {  // near the target (or NaN): FP64
+                double S = 0.0, W = 0.0;
+#pragma unroll
+                for (int t = 0; t < V; ++t) {
+                    if (lane + 32 * t < k) {
+                        const double e = exp(-beta * x[t]);
+                        S += e;
+                        W += e > 0.0 ? e * x[t] : 0.0;  // x = inf: no 0 * inf
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    S += __shfl_xor_sync(kFullA, S, o);
+                    W += __shfl_xor_sync(kFullA, W, o);
+                }
+                // every lane holds the same sums: one lane takes the logarithm
+                if (lane == 0) H = log(S) + beta * (W / S);
+                H = __shfl_sync(kFullA, H, 0);
+            }
             if (fabs(H - target) < 1e-5) break;
             if (H > target) {  // too flat: sharpen
                 lo = beta;
@@ -709,6 +748,7 @@ struct tsne_affinity {
     int knn_kind = 0;             // 0 knn_kernel, 1 knn_tiled_kernel, 2 tensor cores (+ knn_kernel)
     fitsne::KnnTc* tc = nullptr;  // workspace of the tensor-core kNN
     int64_t recomputed = 0;       // queries of the last compute left to knn_kernel
+    int calib_exact = 0;          // 1: every bandwidth step in FP64 (FITSNE_CALIB_FP64=1; same results)
     int64_t Np = 0;               // N rounded up to the candidate tile
     float* Xt = nullptr;          // [D][Np] transposed, zero-padded X
     int32_t* knn_idx = nullptr;   // [N k]
@@ -804,6 +844,7 @@ int tsne_affinity_create(int64_t N, int32_t D, int32_t k, void* stream, tsne_aff
         else if (!strcmp(ov, "tiled")) a->knn_kind = fits ? 1 : 0;
         else if (!strcmp(ov, "rows")) a->knn_kind = 0;
     }
+    if (const char* ce = getenv("FITSNE_CALIB_FP64")) a->calib_exact = ce[0] == '1' ? 1 : 0;
     a->Np = (N + fitsne::kTileC - 1) / fitsne::kTileC * fitsne::kTileC;
     int rc = TSNE_OK;
     if (a->knn_kind == 1) rc = aff_alloc(&a->Xt, (size_t)D * (size_t)a->Np, "transposed X");
@@ -892,7 +933,7 @@ int tsne_affinity_compute(tsne_affinity* a, const float* X, double perplexity, t
     // 2. bandwidths
     {
         const int grid = (int)std::min<int64_t>((N + 7) / 8, 16LL * a->sm_count);
-        calibrate_kernel<<<grid, 256, 0, st>>>(a->knn_d2, N, k, log(perplexity), a->pc);
+        calibrate_kernel<<<grid, 256, 0, st>>>(a->knn_d2, N, k, log(perplexity), a->pc, a->calib_exact);
         ACU(cudaGetLastError(), "calibrate launch");
     }
     ACU(cudaEventRecord(a->ev[2], st), "event");

@@ -254,3 +254,27 @@ def test_sampled_rows_at_one_million_points():
             assert cj[pos] == i and val[rp[j] + pos] == v
     assert abs(val.astype(np.float64).sum() - 1.0) < 1e-4
     assert np.all(np.abs(-np.where(pc > 0, pc * np.log(pc), 0).sum(1)[:1000] - np.log(30.0)) < 1.1e-5)
+
+
+@pytest.mark.parametrize("case", ["mixture", "integer_ties", "k256"])
+def test_fp32_prefilter_keeps_the_fp64_bisection_path(case, monkeypatch):
+    """The bandwidth search evaluates each step with FP32 exponentials first
+    and in FP64 only near the target; every decision is the FP64 one, so
+    beta and p_{j|i} are bit for bit those of the all-FP64 search
+    (FITSNE_CALIB_FP64=1): ordinary rows, exact ties with unreachable
+    perplexity (beta doubled to overflow), and k at its maximum."""
+    if case == "mixture":
+        X, k, perp = inputs.mixture(N=5000, n_clusters=7, dim=50, seed=31), 90, 30.0
+    elif case == "integer_ties":
+        rng = np.random.default_rng(32)
+        X = rng.integers(0, 3, size=(2000, 4)).astype(np.float32)
+        X[1000:1200] = X[0:200]
+        k, perp = 30, 10.0
+    else:
+        X, k, perp = inputs.mixture(N=3000, n_clusters=4, dim=10, seed=33), 256, 80.0
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("FITSNE_CALIB_FP64", flag)
+        out[flag] = gpu_affinities(X, perp, k)
+    for a, b in zip(out["1"], out["0"]):
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
