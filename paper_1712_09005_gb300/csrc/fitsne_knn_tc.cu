@@ -147,14 +147,29 @@ constexpr int kSlots = kBuf / 32;  // shortlist entries per lane when a warp hol
 constexpr int kChunk = 32;         // accumulator columns per tensor-memory load
 
 // An upper bound within 256 key units of the r-th smallest (0-based) key
-// the warp holds: a bitwise radix select over the top 24 key bits, then the
-// largest key with that prefix (empty slots hold 0xffffffff; r must be
-// below the number of real keys). At least r + 1 keys are at or below it.
+// the warp holds: a bitwise radix select over the top 24 key bits (from the
+// highest bit where the real keys differ), then the largest key with that
+// prefix (empty slots hold 0xffffffff; r must be below the number of real
+// keys). At least r + 1 keys are at or below it.
 template <int kS>
 __device__ __forceinline__ uint32_t warp_select_bound(const uint32_t (&key)[kS], int r) {
-    uint32_t want = 0u, mask = 0u;
+    // the bits all real keys share decide nothing: start below them
+    uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;
+#pragma unroll
+    for (int j = 0; j < kS; ++j)
+        if (key[j] != 0xFFFFFFFFu) {
+            kmin = min(kmin, key[j]);
+            kmax = max(kmax, key[j]);
+        }
+    kmin = __reduce_min_sync(kFull, kmin);
+    kmax = __reduce_max_sync(kFull, kmax);
+    if (kmin >= kmax) return kmin | 0xFFu;
+    const int h = 31 - __clz(kmin ^ kmax);  // the highest bit where real keys differ
+    if (h < 8) return kmax | 0xFFu;
+    uint32_t mask = ~((2u << h) - 1u);       // the shared bits (none when h = 31)
+    uint32_t want = kmin & mask;
 #pragma unroll 1
-    for (int bit = 31; bit >= 8; --bit) {
+    for (int bit = h; bit >= 8; --bit) {
         const uint32_t m2 = mask | (1u << bit);
         unsigned c = 0u;
 #pragma unroll
