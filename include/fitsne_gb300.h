@@ -454,16 +454,15 @@ void* tsne_batch_stream(const tsne_batch* batch);
  * neighbours (1..256, k < N, 2 N k < 2^31); all device memory (about
  * 40 N k bytes) is allocated here; work is enqueued on stream (cudaStream_t,
  * NULL = legacy default). INVALID_ARG on bad sizes, OOM. The kNN kernel is
- * chosen here: from N = 32,768 the tensor-core one (tcgen05 tiles of
- * 128 x 128 approximate distances shortlist the candidates; the shortlist
- * gets the exact FP32 distances; queries whose shortlist is not provably
- * complete are recomputed by the row kernel; it needs about 1040 + 8 S
- * bytes more device memory per point, S = 2 k + 32 rounded up to 64, 128,
- * 256 or 512, plus 512 KB per SM); below it the register-tiled one for N >= 400,000
- * where its shared memory (D, k) fits (never, with the default threshold),
- * else the one-candidate-per-lane one. The environment variable
- * FITSNE_KNN_KERNEL=tc, =tiled or =rows, read at create, overrides the size
- * rule (all three give the same lists and distances, bit for bit).
+ * chosen here: the tensor-core one (tcgen05 tiles of 128 x 128
+ * approximate distances shortlist the candidates; the shortlist gets the
+ * exact FP32 distances; queries whose shortlist is not provably complete
+ * are recomputed by the row kernel; it needs about 1040 + 8 S bytes more
+ * device memory per point, S = 2 k + 32 rounded up to 64, 128, 256 or 512,
+ * plus 512 KB per SM). The environment variable FITSNE_KNN_KERNEL=tiled or
+ * =rows, read at create, selects the register-tiled FP32 kernel (where its
+ * shared memory (D, k) fits) or the one-candidate-per-lane one instead (all
+ * three give the same lists and distances, bit for bit).
  * tsne_affinity_compute: X is DEVICE memory, N x D row-major FP32, read
  * only; 1 <= perplexity <= k. Writes into *P_out a CSR that points into the
  * workspace: valid until the next compute or destroy, owned by the
